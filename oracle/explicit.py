@@ -1,0 +1,48 @@
+"""Explicit zero-padded FFT convolution in FP64 (the paper's comparison method).
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
+
+Explicit dealiasing pads every input with zeros to a length N >= M, takes
+length-N FFTs, applies ``mult`` pointwise and inverse transforms (Section 1,
+Section 6).  numpy's FFT is the FFT step.  For centered data the zero
+padding is applied symmetrically by transforming at the centered offsets;
+for Hermitian data the expanded symmetric array is used.  Used as the
+full-field oracle of the multidimensional workloads, where the direct sum is
+too slow, and pinned against the direct sum on small grids.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .direct import hermitian_expand_nd
+
+
+def _pairs(n, mult):
+    return [(0, 1)] if mult == "product" else [(0, 1), (1, 2), (2, 0)]
+
+
+def convnd_explicit(fs, kinds, Ns, mult="product") -> np.ndarray:
+    """N-D convolution by explicit padding to sizes Ns (one per axis)."""
+    fs = [np.asarray(f, dtype=np.complex128) for f in fs]
+    herm = kinds[-1] == "hermitian"
+    if herm:
+        H = fs[0].shape[-1]
+        ex = [hermitian_expand_nd(f, f.shape[:-1]) for f in fs]
+        lo = [-(fs[0].shape[a] // 2) if kinds[a] == "centered" else 0 for a in range(len(kinds) - 1)] + [-(H - 1)]
+    else:
+        ex = fs
+        lo = [-(fs[0].shape[a] // 2) if kinds[a] == "centered" else 0 for a in range(len(kinds))]
+    axes = tuple(range(len(kinds)))
+    # place each array at its (possibly negative) centered offsets modulo N
+    padded = []
+    for e in ex:
+        P = np.zeros(tuple(Ns), dtype=np.complex128)
+        idx = np.ix_(*[np.mod(np.arange(e.shape[a]) + lo[a], Ns[a]) for a in axes])
+        P[idx] = e
+        padded.append(np.fft.fftn(P, axes=axes))
+    spec = sum(padded[i] * padded[j] for i, j in _pairs(len(padded), mult))
+    full = np.fft.ifftn(spec, axes=axes)
+    out_lo = lo[:-1] + [0] if herm else lo
+    out_shape = fs[0].shape
+    idx = np.ix_(*[np.mod(np.arange(out_shape[a]) + out_lo[a], Ns[a]) for a in axes])
+    return full[idx]
