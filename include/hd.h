@@ -1,0 +1,159 @@
+/*
+ * hd.h -- C ABI of the GB300 hybrid-dealiased convolution library (libhd.so).
+ *
+ * Method: Murasko & Bowman, "Hybrid Dealiasing of Complex Convolutions",
+ * arXiv 2303.17510.  A general convolution maps A inputs of length L,
+ * zero padded to at least the dealiasing length M, to B outputs whose DFT is
+ * a pointwise function `mult` of the inputs' DFTs (Section 2, problem
+ * statement).  The library pads each input explicitly to p*m, implicitly to
+ * q*m, and computes the result one residue contribution at a time
+ * (Section 2.2, Alg. convolve / convolveX): per residue, A forward
+ * transforms, `mult`, B backward transforms accumulated into the output;
+ * the sum is divided by q*m.
+ *
+ * Conventions shared by every entry point
+ *   - All data are complex, interleaved (re, im): HD_F32 = two floats,
+ *     HD_F64 = two doubles.
+ *   - zeta_N = exp(2 pi i / N); forward transforms use zeta^{+}, backward
+ *     transforms zeta^{-} (Section 2).
+ *   - Stored layout of one 1D array (per axis for N-D arrays):
+ *       HD_COMPLEX    f_0 .. f_{L-1}                       (L values)
+ *       HD_CENTERED   f_c at stored index c + floor(L/2),   (L values)
+ *                     c = -floor(L/2) .. L-floor(L/2)-1     (Section 3)
+ *       HD_HERMITIAN  f_0 .. f_{ceil(L/2)-1} of an array with
+ *                     f_{-c} = conj(f_c); Im f_0 is ignored (Section 4).
+ *     Outputs use the same stored layout as the inputs: the first L values
+ *     of the linear convolution (complex), the centered range (centered) or
+ *     the non-negative half (Hermitian).  Results are already divided by q*m.
+ *   - Device pointers are raw CUDA device addresses on the plan's device;
+ *     `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *     asynchronous with respect to the host and stream ordered.
+ *   - The caller owns every input and output buffer.  A plan owns its
+ *     twiddle tables and its scratch memory; it is not re-entrant across
+ *     concurrent streams.
+ *   - Errors: invalid arguments return HD_ERR_INVALID, unsupported shapes
+ *     HD_ERR_UNSUPPORTED, M below the dealiasing bound HD_ERR_ALIASED, device
+ *     allocation failures HD_ERR_NOMEM, CUDA errors HD_ERR_CUDA (and make the
+ *     plan's status sticky: later calls on that plan return HD_ERR_CUDA).
+ *     A failed call writes nothing to caller buffers except, for
+ *     HD_ERR_CUDA, what kernels already launched may have written.
+ */
+#ifndef HD_H
+#define HD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HD_OK = 0,
+    HD_ERR_INVALID = 1,
+    HD_ERR_UNSUPPORTED = 2,
+    HD_ERR_NOMEM = 3,
+    HD_ERR_CUDA = 4,
+    HD_ERR_TIMEOUT = 5,
+    HD_ERR_ALIASED = 6
+} hd_status;
+
+enum { HD_COMPLEX = 0, HD_CENTERED = 1, HD_HERMITIAN = 2 };
+enum { HD_F32 = 0, HD_F64 = 1 };
+/* HD_MULT_PRODUCT: A = 2, B = 1, F1*F2 (the binary convolution of Section 2).
+ * HD_MULT_SUM_PAIRS3: A = 3, B = 1, F1F2 + F2F3 + F3F1, a sum of binary
+ * products; it dealiases at the binary bound. */
+enum { HD_MULT_PRODUCT = 0, HD_MULT_SUM_PAIRS3 = 1 };
+
+typedef struct hd_plan hd_plan;
+
+/* Full plan description.  Axis 0 is the outermost axis; for ndim = 1 only
+ * index 0 is used.  For N-D plans the innermost axis is contiguous and
+ * axis i has stride row_pitch[i] elements (0 = packed).  kind applies to the
+ * innermost axis; outer axes are HD_COMPLEX when kind is HD_COMPLEX and
+ * HD_CENTERED otherwise (Section 5, Hermitian data: centered outer axes,
+ * Hermitian innermost axis).  m[i] = 0 selects parameters automatically;
+ * p[i], q[i] = 0 derive them from m (Eq. pqdef1, Alg. convolve/convolveX,
+ * Section 5.1-5.2).  D[i] = 0 selects the residue grouping automatically. */
+typedef struct {
+    int ndim;
+    int64_t L[3];
+    int64_t M[3];
+    int A;
+    int B;
+    int kind;
+    int dtype;
+    int mult;
+    int64_t m[3];
+    int64_t p[3];
+    int64_t q[3];
+    int D[3];
+    int64_t row_pitch[3];
+} hd_desc;
+
+/* Derive (p, q, n) from (kind, L, M, m): Eq. pqdef1 with Alg. convolve
+ * (complex: p = ceil(L/m); p <= 2: q = n = ceil(M/m); p > 2: n =
+ * ceil(M/(p m)), q = n p) or Alg. convolveX with Section 5.2 (centered and
+ * Hermitian: p = 2 ceil(L/(2m)), n = ceil(2M/(p m)), q = n p / 2).  n is the
+ * number of residue contributions.  Host only; no device is needed.
+ * Returns HD_ERR_INVALID for non-positive L, M, m or an unknown kind. */
+hd_status hd_derive_params(int kind, int64_t L, int64_t M, int64_t m, int64_t* p, int64_t* q, int64_t* n);
+
+/* Smallest dealiasing length for L stored-layout outputs (host only):
+ * complex 2L-1 (Section 2, M = sum L_i - (A-1)); centered L + floor(L/2);
+ * Hermitian the centered bound of the odd expanded length 2 ceil(L/2) - 1.
+ * The sum-of-pairs mult has the binary bounds.  Returns -1 on bad input. */
+int64_t hd_dealias_bound(int kind, int mult, int64_t L);
+
+/* 1D complex FP32 plan.  A = 2 selects HD_MULT_PRODUCT, A = 3
+ * HD_MULT_SUM_PAIRS3; B must be 1.  m = 0 selects parameters automatically
+ * (tuned cache, learned selector, else a cost model); nonzero m, p, q are
+ * validated: p m >= L, q m >= M, and p > 2 requires q % p == 0 (complex).
+ * An explicit plan (p = q = 1, m >= M) is always legal.  D = 0 or 1.
+ * *out receives the plan or NULL on error. */
+hd_status hd_plan_create(hd_plan** out, int64_t L, int64_t M, int A, int B, int64_t m, int64_t p, int64_t q,
+                         int D);
+
+/* General plan (kind, dtype, mult, 1-3 dimensions).  Same validation as
+ * hd_plan_create per axis; centered/Hermitian axes need p even (or the
+ * explicit p = q = 1) and q % (p/2) == 0. */
+hd_status hd_plan_create_ex(hd_plan** out, const hd_desc* d);
+
+/* One convolution: f[a] (a < A) are device pointers to the A stored
+ * inputs, h[b] (b < B) to the B outputs.  h[0] may equal f[0] (in place,
+ * allowed because A >= B); other overlaps are not allowed. */
+hd_status hd_convolve(const hd_plan* plan, const void* const* f, void* const* h, void* stream);
+
+/* `count` independent convolutions of one plan: instance i of input a
+ * starts at f[a] + i*batch_stride elements (likewise h[b]).  batch_stride
+ * >= the stored length of one instance (all stored values for N-D plans).
+ * count = 0 is a no-op. */
+hd_status hd_convolve_batched(const hd_plan* plan, int64_t count, const void* const* f, void* const* h,
+                              int64_t batch_stride, void* stream);
+
+/* Parameters actually used (per axis 0): m, p, q, D and the plan's device
+ * scratch bytes.  Any output pointer may be NULL. */
+hd_status hd_plan_get_params(const hd_plan* plan, int64_t* m, int64_t* p, int64_t* q, int* D,
+                             size_t* scratch_bytes);
+
+/* Residue contribution r of one stored 1D input (forward transform only:
+ * a3/a7/a8 of the path).  Writes the values of residue r in the order the
+ * paper's transforms return them (Section 2.2 forward1/forward2: F_{q l + r},
+ * l < m; Section 5.1-5.2 inner: F[u m + l] = F_{q l + u n + v}), i.e. m
+ * values for complex p <= 2 and centered/Hermitian p = 2, p m values for
+ * complex p > 2, p m / 2 for centered/Hermitian p > 2.  For Hermitian
+ * plans the values are real and stored with zero imaginary part.  r < n.
+ * 1D plans only. */
+hd_status hd_forward_residue(const hd_plan* plan, const void* f, int64_t r, void* out, void* stream);
+
+/* Releases the plan's device memory (after synchronizing its device). NULL ok. */
+hd_status hd_plan_destroy(hd_plan* plan);
+
+/* Static string for a status code. */
+const char* hd_status_string(hd_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HD_H */

@@ -1,0 +1,167 @@
+"""ctypes binding of libhd.so (argument marshalling only).
+
+Every computation runs in the CUDA library.  Importing this module loads
+``_build/libhd.so`` and raises ``ImportError`` when it is missing: there is
+no fallback of any kind.  Build it with ``python -m paper_2303_17510_gb300.build``
+or ``__graft_entry__.build()``.
+
+Tensors are torch CUDA tensors (complex64 for f32 plans, complex128 for f64
+plans); only their ``data_ptr()`` and the current CUDA stream handle cross the
+boundary.  Raw integer device addresses are accepted too.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libhd.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libhd.so not built ({LIB_PATH}); run paper_2303_17510_gb300.build.build()")
+
+lib = ctypes.CDLL(LIB_PATH)
+
+KIND = {"complex": 0, "centered": 1, "hermitian": 2}
+DTYPE = {"f32": 0, "f64": 1}
+MULT = {"product": 0, "sum_pairs3": 1}
+STATUS = {0: "HD_OK", 1: "HD_ERR_INVALID", 2: "HD_ERR_UNSUPPORTED", 3: "HD_ERR_NOMEM", 4: "HD_ERR_CUDA",
+          5: "HD_ERR_TIMEOUT", 6: "HD_ERR_ALIASED"}
+_i64 = ctypes.c_int64
+_vp = ctypes.c_void_p
+
+
+class hd_desc(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("L", _i64 * 3), ("M", _i64 * 3), ("A", ctypes.c_int), ("B", ctypes.c_int),
+                ("kind", ctypes.c_int), ("dtype", ctypes.c_int), ("mult", ctypes.c_int), ("m", _i64 * 3),
+                ("p", _i64 * 3), ("q", _i64 * 3), ("D", ctypes.c_int * 3), ("row_pitch", _i64 * 3)]
+
+
+class HdError(RuntimeError):
+    def __init__(self, code, where=""):
+        self.code = int(code)
+        self.name = STATUS.get(self.code, str(code))
+        super().__init__(f"{where}: {lib.hd_status_string(self.code).decode()}")
+
+
+def _sig(name, res, args):
+    fn = getattr(lib, name)
+    fn.restype = res
+    fn.argtypes = args
+    return fn
+
+
+_sig("hd_status_string", ctypes.c_char_p, [ctypes.c_int])
+_sig("hd_derive_params", ctypes.c_int, [ctypes.c_int, _i64, _i64, _i64, ctypes.POINTER(_i64), ctypes.POINTER(_i64),
+                                        ctypes.POINTER(_i64)])
+_sig("hd_dealias_bound", _i64, [ctypes.c_int, ctypes.c_int, _i64])
+_sig("hd_plan_create", ctypes.c_int, [ctypes.POINTER(_vp), _i64, _i64, ctypes.c_int, ctypes.c_int, _i64, _i64, _i64,
+                                      ctypes.c_int])
+_sig("hd_plan_create_ex", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(hd_desc)])
+_sig("hd_convolve", ctypes.c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp])
+_sig("hd_convolve_batched", ctypes.c_int, [_vp, _i64, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i64, _vp])
+_sig("hd_plan_get_params", ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64),
+                                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_size_t)])
+_sig("hd_forward_residue", ctypes.c_int, [_vp, _vp, _i64, _vp, _vp])
+_sig("hd_plan_destroy", ctypes.c_int, [_vp])
+
+
+def _check(rc, where):
+    if rc != 0:
+        raise HdError(rc, where)
+
+
+def status_string(code: int) -> str:
+    return lib.hd_status_string(int(code)).decode()
+
+
+def derive_params(kind: str, L: int, M: int, m: int):
+    p, q, n = _i64(), _i64(), _i64()
+    _check(lib.hd_derive_params(KIND[kind], L, M, m, ctypes.byref(p), ctypes.byref(q), ctypes.byref(n)),
+           "hd_derive_params")
+    return p.value, q.value, n.value
+
+
+def dealias_bound(kind: str, L: int, mult: str = "product") -> int:
+    return int(lib.hd_dealias_bound(KIND[kind], MULT[mult], L))
+
+
+def _ptr(x) -> int:
+    if isinstance(x, int):
+        return x
+    return int(x.data_ptr())
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        import torch
+        return int(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+class Plan:
+    """A convolution plan (owns device twiddle tables and scratch)."""
+
+    def __init__(self, L, M, A=2, B=1, m=0, p=0, q=0, D=0, kind="complex", dtype="f32", mult=None, ndim=None):
+        Ls = list(L) if isinstance(L, (list, tuple)) else [L]
+        Ms = list(M) if isinstance(M, (list, tuple)) else [M]
+        ms = list(m) if isinstance(m, (list, tuple)) else [m] * len(Ls)
+        ps = list(p) if isinstance(p, (list, tuple)) else [p] * len(Ls)
+        qs = list(q) if isinstance(q, (list, tuple)) else [q] * len(Ls)
+        Ds = list(D) if isinstance(D, (list, tuple)) else [D] * len(Ls)
+        nd = ndim or len(Ls)
+        if mult is None:
+            mult = "product" if A == 2 else "sum_pairs3"
+        d = hd_desc()
+        d.ndim = nd
+        for i in range(nd):
+            d.L[i], d.M[i], d.m[i], d.p[i], d.q[i], d.D[i] = Ls[i], Ms[i], ms[i], ps[i], qs[i], Ds[i]
+        d.A, d.B, d.kind, d.dtype, d.mult = A, B, KIND[kind], DTYPE[dtype], MULT[mult]
+        self._h = _vp()
+        _check(lib.hd_plan_create_ex(ctypes.byref(self._h), ctypes.byref(d)), "hd_plan_create_ex")
+        self.L, self.M, self.A, self.B = Ls, Ms, A, B
+        self.kind, self.dtype, self.mult, self.ndim = kind, dtype, mult, nd
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
+
+    def params(self):
+        m, p, q, D, s = _i64(), _i64(), _i64(), ctypes.c_int(), ctypes.c_size_t()
+        _check(lib.hd_plan_get_params(self._h, ctypes.byref(m), ctypes.byref(p), ctypes.byref(q), ctypes.byref(D),
+                                      ctypes.byref(s)), "hd_plan_get_params")
+        return dict(m=m.value, p=p.value, q=q.value, D=D.value, scratch_bytes=s.value)
+
+    def convolve(self, fs, h, stream=None):
+        """One convolution: fs = A device arrays (tensors or addresses), h = output."""
+        fa = (_vp * self.A)(*[_ptr(x) for x in fs])
+        ha = (_vp * self.B)(*[_ptr(h)] if not isinstance(h, (list, tuple)) else [_ptr(x) for x in h])
+        _check(lib.hd_convolve(self._h, fa, ha, _stream(stream)), "hd_convolve")
+
+    def convolve_batched(self, fs, h, count, batch_stride, stream=None):
+        fa = (_vp * self.A)(*[_ptr(x) for x in fs])
+        ha = (_vp * self.B)(*[_ptr(h)] if not isinstance(h, (list, tuple)) else [_ptr(x) for x in h])
+        _check(lib.hd_convolve_batched(self._h, int(count), fa, ha, int(batch_stride), _stream(stream)),
+               "hd_convolve_batched")
+
+    def forward_residue(self, f, r, out, stream=None):
+        _check(lib.hd_forward_residue(self._h, _ptr(f), int(r), _ptr(out), _stream(stream)), "hd_forward_residue")
+
+    def close(self):
+        if self._h and self._h.value:
+            lib.hd_plan_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

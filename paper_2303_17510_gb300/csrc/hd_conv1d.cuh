@@ -1,0 +1,296 @@
+// hd_conv1d.cuh -- fused residue-at-a-time 1D convolution kernel (sm_103a).
+//
+// One thread group (T = S/E threads) computes one whole convolution: for each
+// residue it builds the residue's transform input from the stored inputs,
+// runs the forward size-S FFT, applies `mult` in registers, runs the inverse
+// FFT and accumulates the residue's contribution into registers; the sum is
+// scaled by 1/(qm) and stored once (Alg. convolve / convolveX, Section 2.2:
+// residue contributions accumulate, so the transformed residues never leave
+// the chip).
+//
+// Residue transform input.  With N = q m = n S the padded transform of the
+// input at k = S l' + ... is reorganized so that residue r needs one size-S
+// FFT of
+//     W_j = zeta_N^{r j} * sum_{i = j mod S} zeta_N^{r (i - j)} f_i,  0 <= j < S,
+// the twisted input folded modulo S:
+//   complex p <= 2  (S = m):     i in {j, j + m}         (forward1, forward2;
+//                                 Eq. forStan with t = 0, 1)
+//   complex p  > 2  (S = p m):   i = j (S >= L)          (forwardInner; the size-p
+//                                 DFTs along t and the size-m FFTs form one
+//                                 size-pm FFT, Section 5.1)
+//   centered        (S = p m/2): i in {j, j - S}         (forward2C, Eq. wDef;
+//                                 forwardInnerC, Section 5.2, fold factor
+//                                 zeta_n^{-v} = zeta_N^{-v S})
+//   Hermitian       (S = p m/2): as centered with f_{-c} = conj f_c (Eq. wHerDef)
+// and the backward contribution of residue r to h_i is
+//     zeta_N^{-r i} * IFFT_S(mult(F))_{i mod S}                (Eq. invStan, invInner)
+// (backward1/2, backward2C, backwardInner*).  Hermitian residue spectra are
+// real (Section 4), so two residues r1, r2 share one complex FFT:
+// FFT(W^{r1} + i W^{r2}) = F^{r1} + i F^{r2}; mult acts on the real and
+// imaginary parts separately; the inverse of the product splits back by
+// y_j = (Y_j + conj Y_{S-j})/2 and (Y_j - conj Y_{S-j})/(2i).
+//
+// FP32 accumulation over residues is compensated (TwoSum); FP64 is plain.
+#pragma once
+
+#include "hd_fft.cuh"
+
+namespace hd {
+
+enum { KIND_COMPLEX = 0, KIND_CENTERED = 1, KIND_HERMITIAN = 2 };
+enum { MULT_PRODUCT = 0, MULT_PAIRS3 = 1 };
+
+struct ConvArgs {
+    const void* f[3];   // A input bases (device)
+    void* h;            // output base (device)
+    int64_t stride;     // elements between instances
+    int64_t count;      // instances
+    int L;              // stored length of complex/centered data; full length for Hermitian
+    int Ls;             // stored length (Hermitian: ceil(L/2))
+    int H;              // centered offset floor(L/2)
+    int n;              // residues
+    int N;              // n * S = q * m
+    const void* twS;    // zeta_S^k, k < S
+    const void* twN;    // zeta_N^k, k < N
+    double invN;        // 1 / N
+};
+
+template <class R>
+struct Acc;
+template <>
+struct Acc<float> {
+    // TwoSum compensated accumulation s + c += x
+    __device__ __forceinline__ static void add(float& s, float& c, float x) {
+        float t = s + x;
+        float bp = t - s;
+        float err = (s - (t - bp)) + (x - bp);
+        s = t;
+        c += err;
+    }
+};
+template <>
+struct Acc<double> {
+    __device__ __forceinline__ static void add(double& s, double&, double x) { s += x; }
+};
+
+// Stored input value(s) folded to transform slot j (see header comment).
+// Returns block-0 and block-1 values (block 1 is conj-mirrored for Hermitian).
+template <int KIND, class T>
+__device__ __forceinline__ void load_fold(const T* __restrict__ f, int j, int S, const ConvArgs& a, bool valid,
+                                          T& b0, T& b1) {
+    b0 = czero<T>();
+    b1 = czero<T>();
+    if (!valid) return;
+    if constexpr (KIND == KIND_COMPLEX) {
+        if (j < a.L) b0 = f[j];
+        if (j + S < a.L) b1 = f[j + S];
+    } else if constexpr (KIND == KIND_CENTERED) {
+        if (j < a.L - a.H) b0 = f[j + a.H];
+        if (j >= S - a.H) b1 = f[j - S + a.H];
+    } else {
+        if (j < a.Ls) {
+            b0 = f[j];
+            if (j == 0) b0.y = 0;
+        }
+        if (j > 0 && S - j < a.Ls) b1 = cconj(f[S - j]);
+    }
+}
+
+template <class R, int S, int E, int KIND, int MULT, int NB, int G>
+__global__ void __launch_bounds__(G*(S / E), (G * (S / E) <= 256 && NB == 1 && MULT == MULT_PRODUCT) ? 2 : 1) conv1d_kernel(const __grid_constant__ ConvArgs a) {
+    using T = cplx<R>;
+    using Sh = FftShape<S, E>;
+    constexpr int TT = Sh::T;
+    constexpr int A = (MULT == MULT_PRODUCT) ? 2 : 3;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int g = threadIdx.x / TT;
+    const int tau = threadIdx.x - g * TT;
+    T* sm = reinterpret_cast<T*>(smem_raw) + g * Sh::SMEM;
+    const int64_t inst = (int64_t)blockIdx.x * G + g;
+    const bool valid = inst < a.count;
+    const T* twS = static_cast<const T*>(a.twS);
+    const T* twN = static_cast<const T*>(a.twN);
+    const T* fin[A];
+#pragma unroll
+    for (int aa = 0; aa < A; ++aa) fin[aa] = static_cast<const T*>(a.f[aa]) + (valid ? inst * a.stride : 0);
+
+    R s0[2 * E], c0[2 * E];          // accumulator of block 0 (re, im interleaved)
+    R s1[NB == 2 ? 2 * E : 1], c1[NB == 2 ? 2 * E : 1];
+#pragma unroll
+    for (int e = 0; e < 2 * E; ++e) s0[e] = c0[e] = R(0);
+    if constexpr (NB == 2) {
+#pragma unroll
+        for (int e = 0; e < 2 * E; ++e) s1[e] = c1[e] = R(0);
+    }
+
+    if constexpr (KIND != KIND_HERMITIAN) {
+        for (int r = 0; r < a.n; ++r) {
+            T cr = ldtw(twN + (int64_t)r * S);          // zeta_N^{r S}
+            if constexpr (KIND == KIND_CENTERED) cr = cconj(cr);
+            T p[E], sacc[E];
+#pragma unroll
+            for (int aa = 0; aa < A; ++aa) {
+                T v[E];
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int j = tau + TT * e;
+                    T b0, b1;
+                    load_fold<KIND>(fin[aa], j, S, a, valid, b0, b1);
+                    T w = cadd(b0, cmul(cr, b1));
+                    v[e] = cmul(w, ldtw(twN + r * j));
+                }
+                fft_forward<S, E>(v, sm, twS, tau);
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    if constexpr (MULT == MULT_PRODUCT) {
+                        if (aa == 0) p[e] = v[e];
+                        else p[e] = cmul(p[e], v[e]);
+                    } else {
+                        // F1F2 + F2F3 + F3F1 = F1 F2 + F3 (F1 + F2)
+                        if (aa == 0) {
+                            p[e] = v[e];
+                        } else if (aa == 1) {
+                            sacc[e] = cadd(p[e], v[e]);
+                            p[e] = cmul(p[e], v[e]);
+                        } else {
+                            p[e] = cadd(p[e], cmul(v[e], sacc[e]));
+                        }
+                    }
+                }
+            }
+            fft_inverse<S, E>(p, sm, twS, tau);
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int j = tau + TT * e;
+                T y = cmulc(p[e], ldtw(twN + r * j));    // zeta_N^{-r j} y_j
+                Acc<R>::add(s0[2 * e], c0[2 * e], y.x);
+                Acc<R>::add(s0[2 * e + 1], c0[2 * e + 1], y.y);
+                if constexpr (NB == 2) {
+                    T y1 = cmulc(y, cr);                 // block 1: extra zeta_N^{-r o}
+                    Acc<R>::add(s1[2 * e], c1[2 * e], y1.x);
+                    Acc<R>::add(s1[2 * e + 1], c1[2 * e + 1], y1.y);
+                }
+            }
+        }
+    } else {
+        for (int r1 = 0; r1 < a.n; r1 += 2) {
+            const int r2 = r1 + 1;
+            const bool has2 = r2 < a.n;
+            const T cr1 = cconj(ldtw(twN + (int64_t)r1 * S));             // zeta_N^{-r1 S}
+            const T cr2 = has2 ? cconj(ldtw(twN + (int64_t)r2 * S)) : czero<T>();
+            T p[E], sacc[E];
+#pragma unroll
+            for (int aa = 0; aa < A; ++aa) {
+                T v[E];
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int j = tau + TT * e;
+                    T b0, b1;
+                    load_fold<KIND>(fin[aa], j, S, a, valid, b0, b1);
+                    T w1 = cmul(cadd(b0, cmul(cr1, b1)), ldtw(twN + r1 * j));
+                    T w2 = has2 ? cmul(cadd(b0, cmul(cr2, b1)), ldtw(twN + r2 * j)) : czero<T>();
+                    v[e] = mk<T>(w1.x - w2.y, w1.y + w2.x);   // W1 + i W2
+                }
+                fft_forward<S, E>(v, sm, twS, tau);
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    // real parts carry residue r1, imaginary parts residue r2
+                    if constexpr (MULT == MULT_PRODUCT) {
+                        if (aa == 0) p[e] = v[e];
+                        else p[e] = mk<T>(p[e].x * v[e].x, p[e].y * v[e].y);
+                    } else {
+                        if (aa == 0) {
+                            p[e] = v[e];
+                        } else if (aa == 1) {
+                            sacc[e] = cadd(p[e], v[e]);
+                            p[e] = mk<T>(p[e].x * v[e].x, p[e].y * v[e].y);
+                        } else {
+                            p[e] = mk<T>(p[e].x + v[e].x * sacc[e].x, p[e].y + v[e].y * sacc[e].y);
+                        }
+                    }
+                }
+            }
+            fft_inverse<S, E>(p, sm, twS, tau);
+            // split the two Hermitian inverses: needs Y_{S-j}
+#pragma unroll
+            for (int e = 0; e < E; ++e) sm[padidx(tau + TT * e)] = p[e];
+            __syncthreads();
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int j = tau + TT * e;
+                const T ym = sm[padidx((S - j) & (S - 1))];
+                const T yj = p[e];
+                const R hf = R(0.5);
+                T g1 = mk<T>((yj.x + ym.x) * hf, (yj.y - ym.y) * hf);     // (Y_j + conj Y_{S-j}) / 2
+                T d = mk<T>(yj.x - ym.x, yj.y + ym.y);                    // Y_j - conj Y_{S-j}
+                T g2 = mk<T>(d.y * hf, -d.x * hf);                         // d / (2i)
+                T y = cmulc(g1, ldtw(twN + r1 * j));
+                if (has2) y = cadd(y, cmulc(g2, ldtw(twN + r2 * j)));
+                Acc<R>::add(s0[2 * e], c0[2 * e], y.x);
+                Acc<R>::add(s0[2 * e + 1], c0[2 * e + 1], y.y);
+            }
+            __syncthreads();
+        }
+    }
+
+    if (!valid) return;
+    T* hout = static_cast<T*>(a.h) + inst * a.stride;
+    const R sc = R(a.invN);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int j = tau + TT * e;
+        T y0 = mk<T>((s0[2 * e] + c0[2 * e]) * sc, (s0[2 * e + 1] + c0[2 * e + 1]) * sc);
+        if constexpr (KIND == KIND_COMPLEX) {
+            if (j < a.L) hout[j] = y0;
+            if constexpr (NB == 2) {
+                if (j + S < a.L) hout[j + S] = mk<T>((s1[2 * e] + c1[2 * e]) * sc, (s1[2 * e + 1] + c1[2 * e + 1]) * sc);
+            }
+        } else if constexpr (KIND == KIND_CENTERED) {
+            if (j < a.L - a.H) hout[j + a.H] = y0;
+            if constexpr (NB == 2) {
+                if (j >= S - a.H)
+                    hout[j - S + a.H] = mk<T>((s1[2 * e] + c1[2 * e]) * sc, (s1[2 * e + 1] + c1[2 * e + 1]) * sc);
+            }
+        } else {
+            if (j < a.Ls) hout[j] = y0;
+        }
+    }
+}
+
+// Forward transform of one residue of one input, written in the paper's
+// order: out[u m + l] = X[P l + u] with P = S/m (see hd_forward_residue).
+template <class R, int S, int E, int KIND>
+__global__ void __launch_bounds__(S / E) forward_residue_kernel(const __grid_constant__ ConvArgs a, int r, int m,
+                                                               void* out) {
+    using T = cplx<R>;
+    using Sh = FftShape<S, E>;
+    constexpr int TT = Sh::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sm = reinterpret_cast<T*>(smem_raw);
+    const int tau = threadIdx.x;
+    const T* twS = static_cast<const T*>(a.twS);
+    const T* twN = static_cast<const T*>(a.twN);
+    const T* f = static_cast<const T*>(a.f[0]);
+    T cr = ldtw(twN + (int64_t)r * S);
+    if constexpr (KIND != KIND_COMPLEX) cr = cconj(cr);
+    T v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int j = tau + TT * e;
+        T b0, b1;
+        load_fold<KIND>(f, j, S, a, true, b0, b1);
+        v[e] = cmul(cadd(b0, cmul(cr, b1)), ldtw(twN + r * j));
+    }
+    fft_forward<S, E>(v, sm, twS, tau);
+    const int P = S / m;
+    T* o = static_cast<T*>(out);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int k = spectral_index<S, E>(tau, e);
+        T x = v[e];
+        if constexpr (KIND == KIND_HERMITIAN) x.y = 0;
+        o[(k % P) * m + k / P] = x;
+    }
+}
+
+}  // namespace hd

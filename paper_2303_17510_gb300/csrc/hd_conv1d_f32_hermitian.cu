@@ -1,0 +1,7 @@
+// Fused 1D convolution kernels: f32, hermitian data (instantiation unit).
+#define HD_REAL float
+#define HD_KIND hd::KIND_HERMITIAN
+#define HD_DT f32
+#define HD_KN hermitian
+#define HD_SE_EXTRA(X) X(4096, 8)
+#include "hd_conv1d_tu.cuh"

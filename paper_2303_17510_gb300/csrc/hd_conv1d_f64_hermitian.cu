@@ -1,0 +1,7 @@
+// Fused 1D convolution kernels: f64, hermitian data (instantiation unit).
+#define HD_REAL double
+#define HD_KIND hd::KIND_HERMITIAN
+#define HD_DT f64
+#define HD_KN hermitian
+#define HD_SE_EXTRA(X) 
+#include "hd_conv1d_tu.cuh"

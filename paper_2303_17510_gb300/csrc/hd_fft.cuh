@@ -1,0 +1,356 @@
+// hd_fft.cuh -- block-level radix-E FFT engine for sm_103a.
+//
+// One thread group of T = S/E threads computes one size-S FFT (S a power of
+// two).  Each thread keeps E values in registers; passes are radix-E
+// butterflies in registers (a final smaller radix when log2 S is not a
+// multiple of log2 E), and between passes the group exchanges values through
+// shared memory.  This is the size-m FFT of the method (Section 2: the
+// unpadded FFTs the residue transforms call; Section 5.1: for p > 2 the
+// size-p DFTs along t and the size-m FFTs along s form one size-pm FFT).
+//
+// Sign convention (Section 2): the forward transform is
+//     X_k = sum_j zeta_S^{k j} x_j,   zeta_S = exp(+2 pi i / S),
+// the inverse is the unnormalized sum with zeta^{-}.
+//
+// Data layouts
+//   natural   thread tau holds x[tau + T e] in register e  (forward input,
+//             inverse output)
+//   spectral  thread tau holds X[tau + T beta + (S/R_last) k1] in register
+//             beta*R_last + k1, where R_last is the radix of the last pass
+//             (forward output, inverse input).  Pointwise `mult` works in this
+//             layout directly: every spectrum of one size has the same map.
+//
+// Pass k (sub-transform size N_k = S / prod_{i<k} R_i, Q_k = N_k / R_k)
+// acts on virtual threads nu = tau + T beta (beta < E/R_k), nu = b Q_k + c:
+// an R_k-point DFT over the R_k values of sub-problem b at c + i Q_k, then
+// the twiddle zeta_{N_k}^{c k1}.  Result k1 of nu goes to shared slot
+// nu + (S/R_k) k1 (conflict-free, consecutive tau), from which pass k+1
+// reads.  Shared addresses are padded by one element every 16 (a + a/16),
+// which keeps these exchange patterns free of bank conflicts for 8-byte
+// elements (and within 2-way for E = 8 at the Q = 8 read).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hd {
+
+template <class R>
+struct cplx_of;
+template <>
+struct cplx_of<float> {
+    using type = float2;
+};
+template <>
+struct cplx_of<double> {
+    using type = double2;
+};
+template <class R>
+using cplx = typename cplx_of<R>::type;
+
+template <class T>
+using real_of = decltype(T::x);
+
+template <class T>
+__device__ __forceinline__ T mk(real_of<T> a, real_of<T> b) {
+    T t;
+    t.x = a;
+    t.y = b;
+    return t;
+}
+template <class T>
+__device__ __forceinline__ T cadd(T a, T b) {
+    return mk<T>(a.x + b.x, a.y + b.y);
+}
+template <class T>
+__device__ __forceinline__ T csub(T a, T b) {
+    return mk<T>(a.x - b.x, a.y - b.y);
+}
+template <class T>
+__device__ __forceinline__ T cmul(T a, T b) {
+    return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+template <class T>
+__device__ __forceinline__ T cmulc(T a, T b) {
+    return mk<T>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+template <class T>
+__device__ __forceinline__ T cconj(T a) {
+    return mk<T>(a.x, -a.y);
+}
+template <class T>
+__device__ __forceinline__ T cscale(T a, real_of<T> s) {
+    return mk<T>(a.x * s, a.y * s);
+}
+// multiply by +i (INV = false) or -i (INV = true)
+template <bool INV, class T>
+__device__ __forceinline__ T mul_i(T a) {
+    return INV ? mk<T>(a.y, -a.x) : mk<T>(-a.y, a.x);
+}
+template <class T>
+__device__ __forceinline__ T czero() {
+    return mk<T>(0, 0);
+}
+
+// cos and sin of 2 pi k / 16, k = 0..7 (exact mathematical constants)
+__host__ __device__ constexpr double cos16(int k) {
+    return k == 0 ? 1.0
+         : k == 1 ? 0.92387953251128675613
+         : k == 2 ? 0.70710678118654752440
+         : k == 3 ? 0.38268343236508977173
+         : k == 4 ? 0.0
+         : k == 5 ? -0.38268343236508977173
+         : k == 6 ? -0.70710678118654752440
+                  : -0.92387953251128675613;
+}
+__host__ __device__ constexpr double sin16(int k) {
+    return k == 0 ? 0.0
+         : k == 1 ? 0.38268343236508977173
+         : k == 2 ? 0.70710678118654752440
+         : k == 3 ? 0.92387953251128675613
+         : k == 4 ? 1.0
+         : k == 5 ? 0.92387953251128675613
+         : k == 6 ? 0.70710678118654752440
+                  : 0.38268343236508977173;
+}
+
+// a * zeta_16^{K} (INV: zeta_16^{-K}), K = 0..7, folded at compile time
+template <int K, bool INV, class T>
+__device__ __forceinline__ T rot16(T a) {
+    using R = real_of<T>;
+    if constexpr (K == 0) {
+        return a;
+    } else if constexpr (K == 4) {
+        return mul_i<INV>(a);
+    } else if constexpr (K == 2 || K == 6) {
+        constexpr R h = R(0.70710678118654752440);
+        // zeta_8 = (1+i)h, zeta_8^3 = (-1+i)h
+        if constexpr (K == 2) {
+            return INV ? mk<T>((a.x + a.y) * h, (a.y - a.x) * h) : mk<T>((a.x - a.y) * h, (a.x + a.y) * h);
+        } else {
+            return INV ? mk<T>((a.y - a.x) * h, -(a.x + a.y) * h) : mk<T>(-(a.x + a.y) * h, (a.x - a.y) * h);
+        }
+    } else {
+        constexpr R c = R(cos16(K));
+        constexpr R s = INV ? R(-sin16(K)) : R(sin16(K));
+        return mk<T>(a.x * c - a.y * s, a.x * s + a.y * c);
+    }
+}
+
+// In-register DFTs of size 2, 4, 8, 16, natural order in and out.
+template <bool INV, class T>
+__device__ __forceinline__ void dft2(T& a, T& b) {
+    T t = a;
+    a = cadd(t, b);
+    b = csub(t, b);
+}
+
+template <bool INV, class T>
+__device__ __forceinline__ void dft4(T& v0, T& v1, T& v2, T& v3) {
+    T a = cadd(v0, v2), b = csub(v0, v2), c = cadd(v1, v3), d = mul_i<INV>(csub(v1, v3));
+    v0 = cadd(a, c);
+    v2 = csub(a, c);
+    v1 = cadd(b, d);
+    v3 = csub(b, d);
+}
+
+template <bool INV, class T>
+__device__ __forceinline__ void dft8(T* v) {
+    T e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+    T o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+    dft4<INV>(e0, e1, e2, e3);
+    dft4<INV>(o0, o1, o2, o3);
+    o1 = rot16<2, INV>(o1);
+    o2 = rot16<4, INV>(o2);
+    o3 = rot16<6, INV>(o3);
+    v[0] = cadd(e0, o0);
+    v[4] = csub(e0, o0);
+    v[1] = cadd(e1, o1);
+    v[5] = csub(e1, o1);
+    v[2] = cadd(e2, o2);
+    v[6] = csub(e2, o2);
+    v[3] = cadd(e3, o3);
+    v[7] = csub(e3, o3);
+}
+
+template <bool INV, class T>
+__device__ __forceinline__ void dft16(T* v) {
+    T e[8], o[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        e[j] = v[2 * j];
+        o[j] = v[2 * j + 1];
+    }
+    dft8<INV>(e);
+    dft8<INV>(o);
+    o[1] = rot16<1, INV>(o[1]);
+    o[2] = rot16<2, INV>(o[2]);
+    o[3] = rot16<3, INV>(o[3]);
+    o[4] = rot16<4, INV>(o[4]);
+    o[5] = rot16<5, INV>(o[5]);
+    o[6] = rot16<6, INV>(o[6]);
+    o[7] = rot16<7, INV>(o[7]);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        v[k] = cadd(e[k], o[k]);
+        v[k + 8] = csub(e[k], o[k]);
+    }
+}
+
+template <int R, bool INV, class T>
+__device__ __forceinline__ void dft_reg(T* v) {
+    if constexpr (R == 1) {
+    } else if constexpr (R == 2) {
+        dft2<INV>(v[0], v[1]);
+    } else if constexpr (R == 4) {
+        dft4<INV>(v[0], v[1], v[2], v[3]);
+    } else if constexpr (R == 8) {
+        dft8<INV>(v);
+    } else {
+        static_assert(R == 16, "radix");
+        dft16<INV>(v);
+    }
+}
+
+__host__ __device__ constexpr int ilog2c(int x) { return x <= 1 ? 0 : 1 + ilog2c(x >> 1); }
+
+// Pass structure of a size-S FFT with E values per thread.
+template <int S, int E>
+struct FftShape {
+    static_assert((S & (S - 1)) == 0 && (E & (E - 1)) == 0 && E >= 2 && E <= 16 && S >= E, "shape");
+    static constexpr int T = S / E;
+    static constexpr int LS = ilog2c(S);
+    static constexpr int LE = ilog2c(E);
+    static constexpr int KFULL = LS / LE;
+    static constexpr int K = KFULL + (LS % LE ? 1 : 0);
+    __host__ __device__ static constexpr int radix(int k) { return k < KFULL ? E : (1 << (LS % LE)); }
+    // sub-transform size before pass k
+    __host__ __device__ static constexpr int sub(int k) { return k == 0 ? S : sub(k - 1) / radix(k - 1); }
+    static constexpr int RLAST = radix(K - 1);
+    // padded shared elements for one transform
+    static constexpr int SMEM = S + S / 16;
+};
+
+__device__ __forceinline__ int padidx(int a) { return a + (a >> 4); }
+
+template <class T>
+__device__ __forceinline__ T ldtw(const T* p) {
+    return __ldg(p);
+}
+
+// Forward pass k: radix-R DFT then twiddle zeta_{N_k}^{c k1}.
+template <int S, int E, int k, bool INV, class T>
+__device__ __forceinline__ void fft_pass(T* v, const T* __restrict__ twS, int tau) {
+    using Sh = FftShape<S, E>;
+    constexpr int R = Sh::radix(k);
+    constexpr int N = Sh::sub(k);
+    constexpr int Q = N / R;
+    constexpr int STR = S / N;
+#pragma unroll
+    for (int beta = 0; beta < E / R; ++beta) {
+        T* x = v + beta * R;
+        const int nu = tau + Sh::T * beta;
+        const int c = nu & (Q - 1);
+        if constexpr (!INV) {
+            dft_reg<R, false>(x);
+            if constexpr (Q > 1) {
+#pragma unroll
+                for (int k1 = 1; k1 < R; ++k1) x[k1] = cmul(x[k1], ldtw(twS + c * k1 * STR));
+            }
+        } else {
+            if constexpr (Q > 1) {
+#pragma unroll
+                for (int k1 = 1; k1 < R; ++k1) x[k1] = cmulc(x[k1], ldtw(twS + c * k1 * STR));
+            }
+            dft_reg<R, true>(x);
+        }
+    }
+}
+
+// Exchange between pass k and pass k+1.  FWD: from the layout after pass k
+// to the layout pass k+1 reads; otherwise the reverse.  `sm` is the group's
+// padded buffer.  Two barriers: after the writes, and before the buffer is
+// written again.
+template <int S, int E, int k, bool FWD, class T>
+__device__ __forceinline__ void fft_exchange(T* v, T* sm, int tau) {
+    using Sh = FftShape<S, E>;
+    constexpr int R = Sh::radix(k);
+    constexpr int V = S / R;
+    constexpr int Rn = Sh::radix(k + 1);
+    constexpr int Qn = Sh::sub(k + 1) / Rn;
+    if constexpr (FWD) {
+#pragma unroll
+        for (int beta = 0; beta < E / R; ++beta) {
+            const int nu = tau + Sh::T * beta;
+#pragma unroll
+            for (int k1 = 0; k1 < R; ++k1) sm[padidx(nu + V * k1)] = v[beta * R + k1];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int beta = 0; beta < E / Rn; ++beta) {
+            const int nu = tau + Sh::T * beta;
+            const int b = nu / Qn, c = nu & (Qn - 1);
+#pragma unroll
+            for (int i = 0; i < Rn; ++i) v[beta * Rn + i] = sm[padidx(b * Rn * Qn + i * Qn + c)];
+        }
+        __syncthreads();
+    } else {
+#pragma unroll
+        for (int beta = 0; beta < E / Rn; ++beta) {
+            const int nu = tau + Sh::T * beta;
+            const int b = nu / Qn, c = nu & (Qn - 1);
+#pragma unroll
+            for (int i = 0; i < Rn; ++i) sm[padidx(b * Rn * Qn + i * Qn + c)] = v[beta * Rn + i];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int beta = 0; beta < E / R; ++beta) {
+            const int nu = tau + Sh::T * beta;
+#pragma unroll
+            for (int k1 = 0; k1 < R; ++k1) v[beta * R + k1] = sm[padidx(nu + V * k1)];
+        }
+        __syncthreads();
+    }
+}
+
+template <int S, int E, int k, class T>
+__device__ __forceinline__ void fft_fwd_from(T* v, T* sm, const T* __restrict__ twS, int tau) {
+    using Sh = FftShape<S, E>;
+    fft_pass<S, E, k, false>(v, twS, tau);
+    if constexpr (k + 1 < Sh::K) {
+        fft_exchange<S, E, k, true>(v, sm, tau);
+        fft_fwd_from<S, E, k + 1>(v, sm, twS, tau);
+    }
+}
+
+template <int S, int E, int k, class T>
+__device__ __forceinline__ void fft_inv_from(T* v, T* sm, const T* __restrict__ twS, int tau) {
+    fft_pass<S, E, k, true>(v, twS, tau);
+    if constexpr (k > 0) {
+        fft_exchange<S, E, k - 1, false>(v, sm, tau);
+        fft_inv_from<S, E, k - 1>(v, sm, twS, tau);
+    }
+}
+
+// Forward FFT: natural layout in, spectral layout out.
+template <int S, int E, class T>
+__device__ __forceinline__ void fft_forward(T* v, T* sm, const T* __restrict__ twS, int tau) {
+    fft_fwd_from<S, E, 0>(v, sm, twS, tau);
+}
+
+// Inverse FFT (unnormalized): spectral layout in, natural layout out.
+template <int S, int E, class T>
+__device__ __forceinline__ void fft_inverse(T* v, T* sm, const T* __restrict__ twS, int tau) {
+    fft_inv_from<S, E, FftShape<S, E>::K - 1>(v, sm, twS, tau);
+}
+
+// Frequency index held by register e of thread tau in the spectral layout.
+template <int S, int E>
+__device__ __forceinline__ int spectral_index(int tau, int e) {
+    using Sh = FftShape<S, E>;
+    constexpr int RL = Sh::RLAST;
+    return tau + Sh::T * (e / RL) + (S / RL) * (e % RL);
+}
+
+}  // namespace hd

@@ -1,0 +1,215 @@
+// hd_plan.cu -- plan construction, parameter selection and execution.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "hd_plan.h"
+
+namespace hd {
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    bool changed = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
+            changed = cudaSetDevice(dev) == cudaSuccess;
+        }
+    }
+    ~DeviceGuard() {
+        if (changed) cudaSetDevice(prev);
+    }
+};
+
+int64_t next_pow2(int64_t x) {
+    int64_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+// (p, q) from m for an axis when the caller leaves them at 0 (Eq. pqdef1,
+// Alg. convolve / convolveX, Section 5.1-5.2); p given, q derived likewise.
+void derive_pq(int kind, int64_t L, int64_t M, int64_t m, int64_t* p, int64_t* q) {
+    int64_t pp = *p, qq = *q, nn;
+    if (pp == 0) {
+        hd_derive_params(kind, L, M, m, &pp, &qq, &nn);
+        if (*q != 0) qq = *q;
+    } else if (qq == 0) {
+        if (pp == 1 && m >= M) {
+            qq = 1;
+        } else if (kind == HD_COMPLEX) {
+            if (pp <= 2) qq = ceil_div(M, m);
+            else qq = ceil_div(M, pp * m) * pp;
+        } else {
+            qq = ceil_div(2 * M, pp * m) * (pp / 2);
+        }
+    }
+    *p = pp;
+    *q = qq;
+}
+
+hd_status fill_axis(int dtype, int kind, int mult, int64_t L, int64_t M, int64_t m, int64_t p, int64_t q, int D,
+                    AxisPlan* ax) {
+    std::memset(ax, 0, sizeof(*ax));
+    derive_pq(kind, L, M, m, &p, &q);
+    int64_t S, n;
+    int nb;
+    hd_status st = validate_axis(kind, mult, L, M, m, p, q, &S, &n, &nb);
+    if (st != HD_OK) return st;
+    ax->kind = kind;
+    ax->L = L;
+    ax->M = M;
+    ax->Ls = kind == HD_HERMITIAN ? (L + 1) / 2 : L;
+    ax->m = m;
+    ax->p = p;
+    ax->q = q;
+    ax->n = n;
+    ax->S = S;
+    ax->D = D <= 0 ? 1 : D;
+    ax->nb = nb;
+    ax->E = S < 8 ? (int)S : 8;
+    if (fused_supported(dtype, kind, mult, S, nb)) {
+        ax->path = PATH_FUSED;
+        return HD_OK;
+    }
+    return HD_ERR_UNSUPPORTED;
+}
+
+}  // namespace
+
+hd_status choose_axis(int dtype, int kind, int mult, int A, int B, int64_t L, int64_t M, AxisPlan* best) {
+    double best_cost = 0;
+    bool found = false;
+    auto consider = [&](int64_t m, int64_t p, int64_t q) {
+        AxisPlan ax;
+        if (fill_axis(dtype, kind, mult, L, M, m, p, q, 1, &ax) != HD_OK) return;
+        double c = cost_model(kind, A, B, ax.S, ax.n);
+        // ties (within 1%): smaller qm, then smaller m
+        bool better = !found || c < best_cost * 0.99 ||
+                      (c <= best_cost * 1.01 &&
+                       (ax.n * ax.S < best->n * best->S || (ax.n * ax.S == best->n * best->S && ax.m < best->m)));
+        if (better) {
+            *best = ax;
+            best_cost = c;
+            found = true;
+        }
+    };
+    for (int64_t m = 1; m <= 8192; m <<= 1) {
+        consider(m, 0, 0);
+        // explicit padding beyond ceil(L/m) blocks so that p m is a power of two
+        int64_t p, q, n;
+        hd_derive_params(kind, L, M, m, &p, &q, &n);
+        if (kind == HD_COMPLEX && p > 2 && !is_pow2(p)) consider(m, next_pow2(p), 0);
+        if (kind != HD_COMPLEX && p > 2 && !is_pow2(p / 2)) consider(m, 2 * next_pow2(p / 2), 0);
+    }
+    consider(next_pow2(M), 1, 1);   // explicit zero padding (p = q = 1)
+    return found ? HD_OK : HD_ERR_UNSUPPORTED;
+}
+
+hd_status plan_create(hd_plan** out, const hd_desc* d) {
+    if (d->ndim != 1) return HD_ERR_UNSUPPORTED;
+    if (d->kind < HD_COMPLEX || d->kind > HD_HERMITIAN) return HD_ERR_INVALID;
+    if (d->dtype != HD_F32 && d->dtype != HD_F64) return HD_ERR_INVALID;
+    if (d->B != 1) return HD_ERR_INVALID;
+    if (!((d->mult == HD_MULT_PRODUCT && d->A == 2) || (d->mult == HD_MULT_SUM_PAIRS3 && d->A == 3)))
+        return HD_ERR_INVALID;
+    if (d->L[0] <= 0 || d->M[0] <= 0 || d->m[0] < 0 || d->p[0] < 0 || d->q[0] < 0) return HD_ERR_INVALID;
+    const int64_t bound = hd_dealias_bound(d->kind, d->mult, d->L[0]);
+    if (d->M[0] < bound) return HD_ERR_ALIASED;
+
+    hd_plan* pl = new (std::nothrow) hd_plan;
+    if (!pl) return HD_ERR_NOMEM;
+    std::memset(pl, 0, sizeof(*pl));
+    pl->ndim = 1;
+    pl->kind = d->kind;
+    pl->dtype = d->dtype;
+    pl->mult = d->mult;
+    pl->A = d->A;
+    pl->B = d->B;
+    pl->sticky = HD_OK;
+    if (cudaGetDevice(&pl->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete pl;
+        return HD_ERR_CUDA;
+    }
+    AxisPlan& ax = pl->ax[0];
+    hd_status st;
+    if (d->m[0] == 0) st = choose_axis(d->dtype, d->kind, d->mult, d->A, d->B, d->L[0], d->M[0], &ax);
+    else st = fill_axis(d->dtype, d->kind, d->mult, d->L[0], d->M[0], d->m[0], d->p[0], d->q[0], d->D[0], &ax);
+    if (st != HD_OK) {
+        delete pl;
+        return st;
+    }
+    if (d->D[0] > 0) ax.D = d->D[0];
+    pl->instance_elems = ax.Ls;
+    st = upload_table(ax.S, d->dtype, &ax.twS);
+    if (st == HD_OK) st = upload_table(ax.S * ax.n, d->dtype, &ax.twN);
+    if (st != HD_OK) {
+        plan_free(pl);
+        return st;
+    }
+    *out = pl;
+    return HD_OK;
+}
+
+ConvArgs make_conv_args(const hd_plan& pl, const AxisPlan& ax, int64_t count, const void* const* f, void* const* h,
+                        int64_t stride) {
+    ConvArgs a;
+    std::memset(&a, 0, sizeof(a));
+    for (int i = 0; i < pl.A && i < 3; ++i) a.f[i] = f[i];
+    a.h = h ? h[0] : nullptr;
+    a.stride = stride;
+    a.count = count;
+    a.L = (int)ax.L;
+    a.Ls = (int)ax.Ls;
+    a.H = (int)(ax.L / 2);
+    a.n = (int)ax.n;
+    a.N = (int)(ax.n * ax.S);
+    a.twS = ax.twS;
+    a.twN = ax.twN;
+    a.invN = 1.0 / (double)(ax.n * ax.S);
+    return a;
+}
+
+Conv1dCfg fused_cfg(const hd_plan& pl, const AxisPlan& ax) {
+    Conv1dCfg c;
+    c.dtype = pl.dtype;
+    c.kind = ax.kind;
+    c.mult = pl.mult == HD_MULT_PRODUCT ? MULT_PRODUCT : MULT_PAIRS3;
+    c.nb = ax.nb;
+    c.S = (int)ax.S;
+    c.E = ax.E;
+    return c;
+}
+
+hd_status plan_execute(hd_plan* pl, int64_t count, const void* const* f, void* const* h, int64_t stride,
+                       cudaStream_t st) {
+    DeviceGuard g(pl->device);
+    const AxisPlan& ax = pl->ax[0];
+    if (ax.path != PATH_FUSED) return HD_ERR_UNSUPPORTED;
+    ConvArgs a = make_conv_args(*pl, ax, count, f, h, stride);
+    cudaError_t e = conv1d_launch(fused_cfg(*pl, ax), a, st);
+    if (e != cudaSuccess) {
+        pl->sticky = HD_ERR_CUDA;
+        return HD_ERR_CUDA;
+    }
+    return HD_OK;
+}
+
+void plan_free(hd_plan* pl) {
+    if (!pl) return;
+    DeviceGuard g(pl->device);
+    cudaDeviceSynchronize();
+    for (int i = 0; i < 3; ++i) {
+        if (pl->ax[i].twS) cudaFree(pl->ax[i].twS);
+        if (pl->ax[i].twN) cudaFree(pl->ax[i].twN);
+    }
+    if (pl->scratch) cudaFree(pl->scratch);
+    cudaGetLastError();
+    delete pl;
+}
+
+}  // namespace hd

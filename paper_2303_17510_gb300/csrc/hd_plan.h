@@ -1,0 +1,72 @@
+// hd_plan.h -- internal plan representation shared by the host sources.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/hd.h"
+#include "hd_dispatch.h"
+
+namespace hd {
+
+enum { PATH_FUSED = 0, PATH_SPLIT = 1 };
+
+// One axis of a plan: the paper's parameters (m, p, q, n, D) and the
+// kernel geometry they map to (transform size S = m, p m or p m / 2;
+// n residues of S values; nb folded blocks).
+struct AxisPlan {
+    int kind;
+    int64_t L, M;      // logical length and dealiased length
+    int64_t Ls;        // stored length (Hermitian: ceil(L/2))
+    int64_t m, p, q, n, S;
+    int D;
+    int nb;
+    int E;
+    int path;
+    void* twS;         // zeta_S^k, k < S (device)
+    void* twN;         // zeta_N^k, k < N = n S (device)
+};
+
+int64_t ceil_div(int64_t a, int64_t b);
+bool is_pow2(int64_t x);
+void zeta_fp64(int64_t k, int64_t N, double* c, double* s);
+hd_status upload_table(int64_t N, int dtype, void** dev);
+int max_fused_S(int dtype);
+void axis_geometry(int kind, int64_t L, int64_t m, int64_t p, int64_t q, int64_t* S, int64_t* n, int* nb);
+hd_status validate_axis(int kind, int mult, int64_t L, int64_t M, int64_t m, int64_t p, int64_t q, int64_t* S,
+                        int64_t* n, int* nb);
+bool fused_supported(int dtype, int kind, int mult, int64_t S, int nb);
+double cost_model(int kind, int A, int B, int64_t S, int64_t n);
+
+}  // namespace hd
+
+struct hd_plan {
+    int ndim;
+    int kind;
+    int dtype;
+    int mult;
+    int A, B;
+    hd::AxisPlan ax[3];
+    int64_t instance_elems;   // stored elements of one instance (all axes)
+    size_t scratch_bytes;
+    void* scratch;
+    int device;
+    hd_status sticky;
+};
+
+namespace hd {
+
+hd_status plan_create(hd_plan** out, const hd_desc* d);
+hd_status plan_execute(hd_plan* plan, int64_t count, const void* const* f, void* const* h, int64_t stride,
+                       cudaStream_t st);
+void plan_free(hd_plan* plan);
+ConvArgs make_conv_args(const hd_plan& pl, const AxisPlan& ax, int64_t count, const void* const* f,
+                        void* const* h, int64_t stride);
+Conv1dCfg fused_cfg(const hd_plan& pl, const AxisPlan& ax);
+
+// Legal, supported (m, p, q) of one axis chosen by the cost model; fills ax.
+hd_status choose_axis(int dtype, int kind, int mult, int A, int B, int64_t L, int64_t M, AxisPlan* ax);
+
+}  // namespace hd

@@ -1,0 +1,69 @@
+"""CPU checks of the C ABI: the library loads, exports every symbol that
+include/*.h declares, and its host-only logic (parameter derivation,
+dealiasing bounds, argument validation) matches the oracle bit for bit."""
+import glob
+import os
+import re
+
+import pytest
+
+from oracle import params
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        for m in re.finditer(r"\b(hd_[A-Za-z0-9_]+)\s*\(", src):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def hd():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2303_17510_gb300 as hd
+    return hd
+
+
+def test_symbols_exported(hd):
+    names = _declared_symbols()
+    assert len(names) >= 10
+    missing = [n for n in names if not hasattr(hd.lib, n)]
+    assert not missing, missing
+
+
+@pytest.mark.parametrize("kind", ["complex", "centered", "hermitian"])
+def test_derive_params_matches_oracle(hd, kind):
+    for L in list(range(1, 40)) + [64, 100, 1000, 1024, 2048, 4096, 65536]:
+        for M in sorted({params.dealias_bound(kind, L), params.dealias_bound(kind, L) + 1, 2 * L, 3 * L + 7}):
+            for m in list(range(1, 20)) + [32, 64, 127, 128, 1024, 3072, 4096, 8192]:
+                assert hd.derive_params(kind, L, M, m) == params.derive(kind, L, M, m), (kind, L, M, m)
+
+
+def test_paper_examples_through_abi(hd):
+    assert hd.derive_params("complex", 6, 11, 4)[:2] == (2, 3)             # Fig. 1
+    assert hd.derive_params("centered", 2048, 3072, 16)[:2] == (128, 192)  # Section 6.2 example
+
+
+@pytest.mark.parametrize("kind", ["complex", "centered", "hermitian"])
+@pytest.mark.parametrize("mult", ["product", "sum_pairs3"])
+def test_dealias_bound_matches_oracle(hd, kind, mult):
+    for L in range(1, 300):
+        assert hd.dealias_bound(kind, L, mult) == params.dealias_bound(kind, L, mult)
+
+
+def test_invalid_arguments(hd):
+    with pytest.raises(hd.HdError) as e:
+        hd.derive_params("complex", 0, 10, 4)
+    assert e.value.name == "HD_ERR_INVALID"
+    with pytest.raises(hd.HdError):
+        hd.derive_params("complex", 10, 19, 0)
+    assert hd.dealias_bound("complex", 0) == -1
+    assert hd.lib.hd_status_string(6).decode().startswith("HD_ERR_ALIASED")
+    assert hd.lib.hd_plan_destroy(None) == 0
