@@ -136,8 +136,8 @@ hd_status hd_convolve_batched(const hd_plan* plan, int64_t count, const void* co
 hd_status hd_plan_get_params(const hd_plan* plan, int64_t* m, int64_t* p, int64_t* q, int* D,
                              size_t* scratch_bytes);
 
-/* Residue contribution r of one stored 1D input (forward transform only:
- * a3/a7/a8 of the path).  Writes the values of residue r in the order the
+/* Residue contribution r of one stored 1D input (the forward residue
+ * transform alone, without mult or the backward transform).  Writes the values of residue r in the order the
  * paper's transforms return them (Section 2.2 forward1/forward2: F_{q l + r},
  * l < m; Section 5.1-5.2 inner: F[u m + l] = F_{q l + u n + v}), i.e. m
  * values for complex p <= 2 and centered/Hermitian p = 2, p m values for
@@ -145,6 +145,48 @@ hd_status hd_plan_get_params(const hd_plan* plan, int64_t* m, int64_t* p, int64_
  * plans the values are real and stored with zero imaginary part.  r < n.
  * 1D plans only. */
 hd_status hd_forward_residue(const hd_plan* plan, const void* f, int64_t r, void* out, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Parameter selection (the paper's optimizer, Section 6: scan m, D and the
+ * transform variant, time each candidate, keep the fastest).
+ * ------------------------------------------------------------------------- */
+
+/* One legal, supported parameter choice for a 1D plan and its kernel
+ * variant: (m, p, q, D) as in the paper; S the size-S FFT each residue uses
+ * (m, p m or p m / 2), n the residue count, E values per thread, minb the
+ * register variant (1 or 2 CTAs per SM), comp compensated residue sums.
+ * ms: measured time of one batched call in milliseconds (0 if untimed). */
+typedef struct {
+    int64_t m, p, q;
+    int D;
+    int64_t S, n;
+    int E, minb, comp;
+    double ms;
+} hd_candidate;
+
+/* Lists the legal, supported candidates of a 1D description (host only; no
+ * device needed).  Writes up to cap entries to out (may be NULL with cap 0)
+ * and the total count to *count. */
+hd_status hd_enumerate_candidates(const hd_desc* d, hd_candidate* out, int cap, int* count);
+
+/* Times every candidate on the current device for a batch of `count`
+ * instances (inputs allocated and freed by the call; `reps` timed launches
+ * each, median kept), fills out[0..*n) with ms set, and records the fastest
+ * in the process-wide tuning cache used by plans with m = 0.  Ties within
+ * 1% prefer the smaller q m, then the smaller m.  best may be NULL. */
+hd_status hd_autotune(const hd_desc* d, int64_t count, int reps, hd_candidate* out, int cap, int* n,
+                      hd_candidate* best);
+
+/* Plan for an explicit candidate (as returned by the two calls above). */
+hd_status hd_plan_create_candidate(hd_plan** out, const hd_desc* d, const hd_candidate* c);
+
+/* Process-wide tuning cache: entries are keyed by (dtype, kind, mult, L, M).
+ * hd_tune_cache_put stores c for the description; hd_tune_cache_get returns
+ * HD_OK and fills c when an entry exists, HD_ERR_INVALID otherwise;
+ * hd_tune_cache_clear empties it. */
+hd_status hd_tune_cache_put(const hd_desc* d, const hd_candidate* c);
+hd_status hd_tune_cache_get(const hd_desc* d, hd_candidate* c);
+hd_status hd_tune_cache_clear(void);
 
 /* Releases the plan's device memory (after synchronizing its device). NULL ok. */
 hd_status hd_plan_destroy(hd_plan* plan);

@@ -37,6 +37,14 @@ class hd_desc(ctypes.Structure):
                 ("p", _i64 * 3), ("q", _i64 * 3), ("D", ctypes.c_int * 3), ("row_pitch", _i64 * 3)]
 
 
+class hd_candidate(ctypes.Structure):
+    _fields_ = [("m", _i64), ("p", _i64), ("q", _i64), ("D", ctypes.c_int), ("S", _i64), ("n", _i64),
+                ("E", ctypes.c_int), ("minb", ctypes.c_int), ("comp", ctypes.c_int), ("ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class HdError(RuntimeError):
     def __init__(self, code, where=""):
         self.code = int(code)
@@ -64,6 +72,15 @@ _sig("hd_plan_get_params", ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POIN
                                           ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_size_t)])
 _sig("hd_forward_residue", ctypes.c_int, [_vp, _vp, _i64, _vp, _vp])
 _sig("hd_plan_destroy", ctypes.c_int, [_vp])
+_sig("hd_enumerate_candidates", ctypes.c_int, [ctypes.POINTER(hd_desc), ctypes.POINTER(hd_candidate), ctypes.c_int,
+                                               ctypes.POINTER(ctypes.c_int)])
+_sig("hd_autotune", ctypes.c_int, [ctypes.POINTER(hd_desc), _i64, ctypes.c_int, ctypes.POINTER(hd_candidate),
+                                   ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(hd_candidate)])
+_sig("hd_plan_create_candidate", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(hd_desc),
+                                                ctypes.POINTER(hd_candidate)])
+_sig("hd_tune_cache_put", ctypes.c_int, [ctypes.POINTER(hd_desc), ctypes.POINTER(hd_candidate)])
+_sig("hd_tune_cache_get", ctypes.c_int, [ctypes.POINTER(hd_desc), ctypes.POINTER(hd_candidate)])
+_sig("hd_tune_cache_clear", ctypes.c_int, [])
 
 
 def _check(rc, where):
@@ -101,28 +118,83 @@ def _stream(stream) -> int:
     return int(stream.cuda_stream)
 
 
+def make_desc(L, M, A=2, B=1, m=0, p=0, q=0, D=0, kind="complex", dtype="f32", mult=None, ndim=None):
+    Ls = list(L) if isinstance(L, (list, tuple)) else [L]
+    Ms = list(M) if isinstance(M, (list, tuple)) else [M]
+    ms = list(m) if isinstance(m, (list, tuple)) else [m] * len(Ls)
+    ps = list(p) if isinstance(p, (list, tuple)) else [p] * len(Ls)
+    qs = list(q) if isinstance(q, (list, tuple)) else [q] * len(Ls)
+    Ds = list(D) if isinstance(D, (list, tuple)) else [D] * len(Ls)
+    nd = ndim or len(Ls)
+    if mult is None:
+        mult = "product" if A == 2 else "sum_pairs3"
+    d = hd_desc()
+    d.ndim = nd
+    for i in range(nd):
+        d.L[i], d.M[i], d.m[i], d.p[i], d.q[i], d.D[i] = Ls[i], Ms[i], ms[i], ps[i], qs[i], Ds[i]
+    d.A, d.B, d.kind, d.dtype, d.mult = A, B, KIND[kind], DTYPE[dtype], MULT[mult]
+    return d
+
+
+def enumerate_candidates(**kw):
+    """Legal, supported parameter candidates of a 1D description (host only)."""
+    d = make_desc(**kw)
+    n = ctypes.c_int()
+    _check(lib.hd_enumerate_candidates(ctypes.byref(d), None, 0, ctypes.byref(n)), "hd_enumerate_candidates")
+    arr = (hd_candidate * max(1, n.value))()
+    _check(lib.hd_enumerate_candidates(ctypes.byref(d), arr, n.value, ctypes.byref(n)), "hd_enumerate_candidates")
+    return [arr[i].as_dict() for i in range(n.value)]
+
+
+def autotune(count, reps=5, **kw):
+    """Times every candidate for a batch of `count`; returns (best, all) as dicts
+    and records the best in the library's tuning cache."""
+    d = make_desc(**kw)
+    arr = (hd_candidate * 256)()
+    n = ctypes.c_int()
+    best = hd_candidate()
+    _check(lib.hd_autotune(ctypes.byref(d), int(count), int(reps), arr, 256, ctypes.byref(n), ctypes.byref(best)),
+           "hd_autotune")
+    return best.as_dict(), [arr[i].as_dict() for i in range(min(n.value, 256))]
+
+
+def tune_cache_put(cand: dict, **kw):
+    d = make_desc(**kw)
+    c = hd_candidate(**{k: cand[k] for k, _ in hd_candidate._fields_})
+    _check(lib.hd_tune_cache_put(ctypes.byref(d), ctypes.byref(c)), "hd_tune_cache_put")
+
+
+def tune_cache_get(**kw):
+    d = make_desc(**kw)
+    c = hd_candidate()
+    if lib.hd_tune_cache_get(ctypes.byref(d), ctypes.byref(c)) != 0:
+        return None
+    return c.as_dict()
+
+
+def tune_cache_clear():
+    lib.hd_tune_cache_clear()
+
+
 class Plan:
     """A convolution plan (owns device twiddle tables and scratch)."""
 
-    def __init__(self, L, M, A=2, B=1, m=0, p=0, q=0, D=0, kind="complex", dtype="f32", mult=None, ndim=None):
-        Ls = list(L) if isinstance(L, (list, tuple)) else [L]
-        Ms = list(M) if isinstance(M, (list, tuple)) else [M]
-        ms = list(m) if isinstance(m, (list, tuple)) else [m] * len(Ls)
-        ps = list(p) if isinstance(p, (list, tuple)) else [p] * len(Ls)
-        qs = list(q) if isinstance(q, (list, tuple)) else [q] * len(Ls)
-        Ds = list(D) if isinstance(D, (list, tuple)) else [D] * len(Ls)
-        nd = ndim or len(Ls)
+    def __init__(self, L, M, A=2, B=1, m=0, p=0, q=0, D=0, kind="complex", dtype="f32", mult=None, ndim=None,
+                 candidate=None):
         if mult is None:
             mult = "product" if A == 2 else "sum_pairs3"
-        d = hd_desc()
-        d.ndim = nd
-        for i in range(nd):
-            d.L[i], d.M[i], d.m[i], d.p[i], d.q[i], d.D[i] = Ls[i], Ms[i], ms[i], ps[i], qs[i], Ds[i]
-        d.A, d.B, d.kind, d.dtype, d.mult = A, B, KIND[kind], DTYPE[dtype], MULT[mult]
+        d = make_desc(L, M, A, B, m, p, q, D, kind, dtype, mult, ndim)
         self._h = _vp()
-        _check(lib.hd_plan_create_ex(ctypes.byref(self._h), ctypes.byref(d)), "hd_plan_create_ex")
-        self.L, self.M, self.A, self.B = Ls, Ms, A, B
-        self.kind, self.dtype, self.mult, self.ndim = kind, dtype, mult, nd
+        if candidate is None:
+            _check(lib.hd_plan_create_ex(ctypes.byref(self._h), ctypes.byref(d)), "hd_plan_create_ex")
+        else:
+            c = hd_candidate(**{k: candidate[k] for k, _ in hd_candidate._fields_})
+            _check(lib.hd_plan_create_candidate(ctypes.byref(self._h), ctypes.byref(d), ctypes.byref(c)),
+                   "hd_plan_create_candidate")
+        self.L = list(L) if isinstance(L, (list, tuple)) else [L]
+        self.M = list(M) if isinstance(M, (list, tuple)) else [M]
+        self.A, self.B = A, B
+        self.kind, self.dtype, self.mult, self.ndim = kind, dtype, mult, d.ndim
 
     @property
     def handle(self) -> int:

@@ -11,6 +11,7 @@ import concurrent.futures as cf
 import glob
 import hashlib
 import os
+import re
 import shutil
 import subprocess
 import sys
@@ -33,18 +34,29 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libhd")
 
 
-def _headers_digest() -> str:
+_INC = re.compile(r'^\s*#\s*include\s+"([^"]+)"', re.M)
+
+
+def _deps_digest(src: str) -> str:
+    """Digest of a source and every quoted header it includes, transitively."""
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) +
-                    glob.glob(os.path.join(INCLUDE, "*.h"))):
+    seen, todo = set(), [os.path.abspath(src)]
+    while todo:
+        p = todo.pop()
+        if p in seen or not os.path.exists(p):
+            continue
+        seen.add(p)
+        txt = open(p, "rb").read()
         h.update(p.encode())
-        h.update(open(p, "rb").read())
+        h.update(txt)
+        for inc in _INC.findall(txt.decode("utf-8", "replace")):
+            todo.append(os.path.abspath(os.path.join(os.path.dirname(p), inc)))
     return h.hexdigest()
 
 
 def _compile(src: str, hdr: str, extra) -> str:
     base = os.path.splitext(os.path.basename(src))[0]
-    key = hashlib.sha256((open(src, "rb").read().hex() + hdr + " ".join(ARCH + FLAGS + extra)).encode()).hexdigest()[:16]
+    key = hashlib.sha256((_deps_digest(src) + " ".join(ARCH + FLAGS + extra)).encode()).hexdigest()[:16]
     obj = os.path.join(OUT_DIR, f"{base}.{key}.o")
     if not os.path.exists(obj):
         tmp = obj + f".tmp{os.getpid()}"
@@ -60,7 +72,7 @@ def build(verbose: bool = False, jobs: int | None = None, extra=None) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
     extra = list(extra or [])
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
-    hdr = _headers_digest()
+    hdr = ""
     jobs = jobs or max(1, min(len(srcs), os.cpu_count() or 1))
     with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
         objs = list(ex.map(lambda s: _compile(s, hdr, extra), srcs))

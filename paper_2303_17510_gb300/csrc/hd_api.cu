@@ -137,10 +137,12 @@ hd_status validate_axis(int kind, int mult, int64_t L, int64_t M, int64_t m, int
     return HD_OK;
 }
 
-bool fused_supported(int dtype, int kind, int mult, int64_t S, int nb) {
+int default_minb(int dtype, int64_t S) { return (dtype == HD_F32 && S <= 2048) ? 2 : 1; }
+
+bool fused_supported(int dtype, int kind, int mult, int64_t S, int nb, int64_t Ls, bool comp, int E, int minb) {
     if (!is_pow2(S) || S < 2 || S > max_fused_S(dtype)) return false;
-    Conv1dCfg c{dtype, kind, mult, nb, (int)S, S < 8 ? (int)S : 8};
-    return conv1d_available(c);
+    Conv1dCfg c{dtype, kind, mult, nb, (int)S, E, comp, minb};
+    return conv1d_available(c, (int)staged_row(Ls));
 }
 
 // FFT work of one convolution in units of S log2 S (model used when no
@@ -171,7 +173,13 @@ namespace hd {
         return fn##_f64_hermitian(__VA_ARGS__);                                              \
     } while (0)
 
-bool conv1d_available(const Conv1dCfg& c) { HD_SEL(conv1d_available, c, c); }
+bool conv1d_available(const Conv1dCfg& c, int ls_pad) { HD_SEL(conv1d_available, c, c, ls_pad); }
+int conv1d_variants(int dtype, int kind, Conv1dCfg* out, int cap) {
+    Conv1dCfg c{};
+    c.dtype = dtype;
+    c.kind = kind;
+    HD_SEL(conv1d_variants, c, out, cap);
+}
 cudaError_t conv1d_launch(const Conv1dCfg& c, const ConvArgs& a, cudaStream_t st) { HD_SEL(conv1d_launch, c, c, a, st); }
 cudaError_t forward_residue_launch(const Conv1dCfg& c, const ConvArgs& a, int r, int m, void* out, cudaStream_t st) {
     HD_SEL(forward_residue_launch, c, c, a, r, m, out, st);

@@ -50,34 +50,31 @@ struct ConvArgs {
     int H;              // centered offset floor(L/2)
     int n;              // residues
     int N;              // n * S = q * m
+    int ls_pad;         // staged row length in shared memory (>= Ls, even)
     const void* twS;    // zeta_S^k, k < S
     const void* twN;    // zeta_N^k, k < N
     double invN;        // 1 / N
 };
 
-template <class R>
-struct Acc;
-template <>
-struct Acc<float> {
-    // TwoSum compensated accumulation s + c += x
-    __device__ __forceinline__ static void add(float& s, float& c, float x) {
-        float t = s + x;
-        float bp = t - s;
-        float err = (s - (t - bp)) + (x - bp);
+// Residue-sum accumulation.  COMP: TwoSum compensated s + c += x (FP32 path);
+// otherwise a plain sum.
+template <class R, bool COMP>
+__device__ __forceinline__ void acc_add(R& s, R& c, R x) {
+    if constexpr (COMP) {
+        R t = s + x;
+        R bp = t - s;
+        R err = (s - (t - bp)) + (x - bp);
         s = t;
         c += err;
+    } else {
+        s += x;
     }
-};
-template <>
-struct Acc<double> {
-    __device__ __forceinline__ static void add(double& s, double&, double x) { s += x; }
-};
+}
 
 // Stored input value(s) folded to transform slot j (see header comment).
 // Returns block-0 and block-1 values (block 1 is conj-mirrored for Hermitian).
 template <int KIND, class T>
-__device__ __forceinline__ void load_fold(const T* __restrict__ f, int j, int S, const ConvArgs& a, bool valid,
-                                          T& b0, T& b1) {
+__device__ __forceinline__ void load_fold(const T* f, int j, int S, const ConvArgs& a, bool valid, T& b0, T& b1) {
     b0 = czero<T>();
     b1 = czero<T>();
     if (!valid) return;
@@ -96,79 +93,101 @@ __device__ __forceinline__ void load_fold(const T* __restrict__ f, int j, int S,
     }
 }
 
-template <class R, int S, int E, int KIND, int MULT, int NB, int G>
-__global__ void __launch_bounds__(G*(S / E), (G * (S / E) <= 256 && NB == 1 && MULT == MULT_PRODUCT) ? 2 : 1) conv1d_kernel(const __grid_constant__ ConvArgs a) {
+// Block size bound: one group of T threads, or up to 256 threads of groups.
+template <int S, int E>
+struct ConvLaunch {
+    static constexpr int T = S / E;
+    static constexpr int MAXT = T > 256 ? T : 256;
+};
+
+// One thread group of T = S/E threads per convolution; G = blockDim.x / T
+// groups per CTA.  Shared memory per group: the A staged inputs (ls_pad values
+// each), then A padded FFT exchange buffers.
+// MINB: CTAs per SM the register allocation must allow (1: up to 255
+// registers for 256 threads; 2: at most 128).
+template <class R, int S, int E, int KIND, int MULT, int NB, bool COMP, int MINB>
+__global__ void __launch_bounds__(ConvLaunch<S, E>::MAXT, MINB) conv1d_kernel(const __grid_constant__ ConvArgs a) {
     using T = cplx<R>;
     using Sh = FftShape<S, E>;
     constexpr int TT = Sh::T;
     constexpr int A = (MULT == MULT_PRODUCT) ? 2 : 3;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int G = blockDim.x / TT;
     const int g = threadIdx.x / TT;
     const int tau = threadIdx.x - g * TT;
-    T* sm = reinterpret_cast<T*>(smem_raw) + g * Sh::SMEM;
+    T* st = reinterpret_cast<T*>(smem_raw) + (size_t)g * (A * a.ls_pad + A * Sh::SMEM);
+    T* sm = st + A * a.ls_pad;
     const int64_t inst = (int64_t)blockIdx.x * G + g;
     const bool valid = inst < a.count;
     const T* twS = static_cast<const T*>(a.twS);
     const T* twN = static_cast<const T*>(a.twN);
-    const T* fin[A];
-#pragma unroll
-    for (int aa = 0; aa < A; ++aa) fin[aa] = static_cast<const T*>(a.f[aa]) + (valid ? inst * a.stride : 0);
 
-    R s0[2 * E], c0[2 * E];          // accumulator of block 0 (re, im interleaved)
-    R s1[NB == 2 ? 2 * E : 1], c1[NB == 2 ? 2 * E : 1];
+    // stage the A inputs of this convolution in shared memory (coalesced)
+    if (valid) {
 #pragma unroll
-    for (int e = 0; e < 2 * E; ++e) s0[e] = c0[e] = R(0);
+        for (int aa = 0; aa < A; ++aa) {
+            const T* src = static_cast<const T*>(a.f[aa]) + inst * a.stride;
+            T* dst = st + aa * a.ls_pad;
+            for (int i = tau; i < a.Ls; i += TT) dst[i] = src[i];
+        }
+    }
+    __syncthreads();
+
+    R s0[2 * E], c0[COMP ? 2 * E : 1];
+    R s1[NB == 2 ? 2 * E : 1], c1[(NB == 2 && COMP) ? 2 * E : 1];
+#pragma unroll
+    for (int e = 0; e < 2 * E; ++e) s0[e] = R(0);
+    if constexpr (COMP) {
+#pragma unroll
+        for (int e = 0; e < 2 * E; ++e) c0[e] = R(0);
+    }
     if constexpr (NB == 2) {
 #pragma unroll
-        for (int e = 0; e < 2 * E; ++e) s1[e] = c1[e] = R(0);
+        for (int e = 0; e < 2 * E; ++e) s1[e] = R(0);
+        if constexpr (COMP) {
+#pragma unroll
+            for (int e = 0; e < 2 * E; ++e) c1[e] = R(0);
+        }
     }
+    R dummy = R(0);
 
     if constexpr (KIND != KIND_HERMITIAN) {
         for (int r = 0; r < a.n; ++r) {
             T cr = ldtw(twN + (int64_t)r * S);          // zeta_N^{r S}
             if constexpr (KIND == KIND_CENTERED) cr = cconj(cr);
-            T p[E], sacc[E];
-#pragma unroll
-            for (int aa = 0; aa < A; ++aa) {
-                T v[E];
-#pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    const int j = tau + TT * e;
-                    T b0, b1;
-                    load_fold<KIND>(fin[aa], j, S, a, valid, b0, b1);
-                    T w = cadd(b0, cmul(cr, b1));
-                    v[e] = cmul(w, ldtw(twN + r * j));
-                }
-                fft_forward<S, E>(v, sm, twS, tau);
-#pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    if constexpr (MULT == MULT_PRODUCT) {
-                        if (aa == 0) p[e] = v[e];
-                        else p[e] = cmul(p[e], v[e]);
-                    } else {
-                        // F1F2 + F2F3 + F3F1 = F1 F2 + F3 (F1 + F2)
-                        if (aa == 0) {
-                            p[e] = v[e];
-                        } else if (aa == 1) {
-                            sacc[e] = cadd(p[e], v[e]);
-                            p[e] = cmul(p[e], v[e]);
-                        } else {
-                            p[e] = cadd(p[e], cmul(v[e], sacc[e]));
-                        }
-                    }
-                }
-            }
-            fft_inverse<S, E>(p, sm, twS, tau);
+            T v[A * E];
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const int j = tau + TT * e;
-                T y = cmulc(p[e], ldtw(twN + r * j));    // zeta_N^{-r j} y_j
-                Acc<R>::add(s0[2 * e], c0[2 * e], y.x);
-                Acc<R>::add(s0[2 * e + 1], c0[2 * e + 1], y.y);
+                const T tw = ldtw(twN + r * j);
+#pragma unroll
+                for (int aa = 0; aa < A; ++aa) {
+                    T b0, b1;
+                    load_fold<KIND>(st + aa * a.ls_pad, j, S, a, valid, b0, b1);
+                    v[aa * E + e] = cmul(cadd(b0, cmul(cr, b1)), tw);
+                }
+            }
+            fft_forward<S, E, A>(v, sm, twS, tau);
+            T p[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                if constexpr (MULT == MULT_PRODUCT) {
+                    p[e] = cmul(v[e], v[E + e]);
+                } else {   // F1F2 + F2F3 + F3F1 = F1 F2 + F3 (F1 + F2)
+                    p[e] = cadd(cmul(v[e], v[E + e]), cmul(v[2 * E + e], cadd(v[e], v[E + e])));
+                }
+            }
+            fft_inverse<S, E, 1>(p, sm, twS, tau);
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int j = tau + TT * e;
+                const T y = cmulc(p[e], ldtw(twN + r * j));    // zeta_N^{-r j} y_j
+                acc_add<R, COMP>(s0[2 * e], COMP ? c0[2 * e] : dummy, y.x);
+                acc_add<R, COMP>(s0[2 * e + 1], COMP ? c0[2 * e + 1] : dummy, y.y);
                 if constexpr (NB == 2) {
-                    T y1 = cmulc(y, cr);                 // block 1: extra zeta_N^{-r o}
-                    Acc<R>::add(s1[2 * e], c1[2 * e], y1.x);
-                    Acc<R>::add(s1[2 * e + 1], c1[2 * e + 1], y1.y);
+                    const T y1 = cmulc(y, cr);                 // block 1: extra zeta_N^{-r o}
+                    acc_add<R, COMP>(s1[2 * e], COMP ? c1[2 * e] : dummy, y1.x);
+                    acc_add<R, COMP>(s1[2 * e + 1], COMP ? c1[2 * e + 1] : dummy, y1.y);
                 }
             }
         }
@@ -178,39 +197,35 @@ __global__ void __launch_bounds__(G*(S / E), (G * (S / E) <= 256 && NB == 1 && M
             const bool has2 = r2 < a.n;
             const T cr1 = cconj(ldtw(twN + (int64_t)r1 * S));             // zeta_N^{-r1 S}
             const T cr2 = has2 ? cconj(ldtw(twN + (int64_t)r2 * S)) : czero<T>();
-            T p[E], sacc[E];
+            T v[A * E];
 #pragma unroll
-            for (int aa = 0; aa < A; ++aa) {
-                T v[E];
+            for (int e = 0; e < E; ++e) {
+                const int j = tau + TT * e;
+                const T t1 = ldtw(twN + r1 * j);
+                const T t2 = has2 ? ldtw(twN + r2 * j) : czero<T>();
 #pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    const int j = tau + TT * e;
+                for (int aa = 0; aa < A; ++aa) {
                     T b0, b1;
-                    load_fold<KIND>(fin[aa], j, S, a, valid, b0, b1);
-                    T w1 = cmul(cadd(b0, cmul(cr1, b1)), ldtw(twN + r1 * j));
-                    T w2 = has2 ? cmul(cadd(b0, cmul(cr2, b1)), ldtw(twN + r2 * j)) : czero<T>();
-                    v[e] = mk<T>(w1.x - w2.y, w1.y + w2.x);   // W1 + i W2
-                }
-                fft_forward<S, E>(v, sm, twS, tau);
-#pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    // real parts carry residue r1, imaginary parts residue r2
-                    if constexpr (MULT == MULT_PRODUCT) {
-                        if (aa == 0) p[e] = v[e];
-                        else p[e] = mk<T>(p[e].x * v[e].x, p[e].y * v[e].y);
-                    } else {
-                        if (aa == 0) {
-                            p[e] = v[e];
-                        } else if (aa == 1) {
-                            sacc[e] = cadd(p[e], v[e]);
-                            p[e] = mk<T>(p[e].x * v[e].x, p[e].y * v[e].y);
-                        } else {
-                            p[e] = mk<T>(p[e].x + v[e].x * sacc[e].x, p[e].y + v[e].y * sacc[e].y);
-                        }
-                    }
+                    load_fold<KIND>(st + aa * a.ls_pad, j, S, a, valid, b0, b1);
+                    const T w1 = cmul(cadd(b0, cmul(cr1, b1)), t1);
+                    const T w2 = cmul(cadd(b0, cmul(cr2, b1)), t2);
+                    v[aa * E + e] = mk<T>(w1.x - w2.y, w1.y + w2.x);   // W1 + i W2
                 }
             }
-            fft_inverse<S, E>(p, sm, twS, tau);
+            fft_forward<S, E, A>(v, sm, twS, tau);
+            // real parts carry residue r1, imaginary parts residue r2
+            T p[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const T x0 = v[e], x1 = v[E + e];
+                if constexpr (MULT == MULT_PRODUCT) {
+                    p[e] = mk<T>(x0.x * x1.x, x0.y * x1.y);
+                } else {
+                    const T x2 = v[2 * E + e];
+                    p[e] = mk<T>(x0.x * x1.x + x2.x * (x0.x + x1.x), x0.y * x1.y + x2.y * (x0.y + x1.y));
+                }
+            }
+            fft_inverse<S, E, 1>(p, sm, twS, tau);
             // split the two Hermitian inverses: needs Y_{S-j}
 #pragma unroll
             for (int e = 0; e < E; ++e) sm[padidx(tau + TT * e)] = p[e];
@@ -221,13 +236,13 @@ __global__ void __launch_bounds__(G*(S / E), (G * (S / E) <= 256 && NB == 1 && M
                 const T ym = sm[padidx((S - j) & (S - 1))];
                 const T yj = p[e];
                 const R hf = R(0.5);
-                T g1 = mk<T>((yj.x + ym.x) * hf, (yj.y - ym.y) * hf);     // (Y_j + conj Y_{S-j}) / 2
-                T d = mk<T>(yj.x - ym.x, yj.y + ym.y);                    // Y_j - conj Y_{S-j}
-                T g2 = mk<T>(d.y * hf, -d.x * hf);                         // d / (2i)
+                const T g1 = mk<T>((yj.x + ym.x) * hf, (yj.y - ym.y) * hf);   // (Y_j + conj Y_{S-j}) / 2
+                const T d = mk<T>(yj.x - ym.x, yj.y + ym.y);                  // Y_j - conj Y_{S-j}
+                const T g2 = mk<T>(d.y * hf, -d.x * hf);                       // d / (2i)
                 T y = cmulc(g1, ldtw(twN + r1 * j));
                 if (has2) y = cadd(y, cmulc(g2, ldtw(twN + r2 * j)));
-                Acc<R>::add(s0[2 * e], c0[2 * e], y.x);
-                Acc<R>::add(s0[2 * e + 1], c0[2 * e + 1], y.y);
+                acc_add<R, COMP>(s0[2 * e], COMP ? c0[2 * e] : dummy, y.x);
+                acc_add<R, COMP>(s0[2 * e + 1], COMP ? c0[2 * e + 1] : dummy, y.y);
             }
             __syncthreads();
         }
@@ -239,20 +254,27 @@ __global__ void __launch_bounds__(G*(S / E), (G * (S / E) <= 256 && NB == 1 && M
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         const int j = tau + TT * e;
-        T y0 = mk<T>((s0[2 * e] + c0[2 * e]) * sc, (s0[2 * e + 1] + c0[2 * e + 1]) * sc);
+        const R x0 = COMP ? s0[2 * e] + c0[2 * e] : s0[2 * e];
+        const R y0 = COMP ? s0[2 * e + 1] + c0[2 * e + 1] : s0[2 * e + 1];
+        const T o0 = mk<T>(x0 * sc, y0 * sc);
+        T o1 = czero<T>();
+        if constexpr (NB == 2) {
+            const R x1 = COMP ? s1[2 * e] + c1[2 * e] : s1[2 * e];
+            const R y1 = COMP ? s1[2 * e + 1] + c1[2 * e + 1] : s1[2 * e + 1];
+            o1 = mk<T>(x1 * sc, y1 * sc);
+        }
         if constexpr (KIND == KIND_COMPLEX) {
-            if (j < a.L) hout[j] = y0;
+            if (j < a.L) hout[j] = o0;
             if constexpr (NB == 2) {
-                if (j + S < a.L) hout[j + S] = mk<T>((s1[2 * e] + c1[2 * e]) * sc, (s1[2 * e + 1] + c1[2 * e + 1]) * sc);
+                if (j + S < a.L) hout[j + S] = o1;
             }
         } else if constexpr (KIND == KIND_CENTERED) {
-            if (j < a.L - a.H) hout[j + a.H] = y0;
+            if (j < a.L - a.H) hout[j + a.H] = o0;
             if constexpr (NB == 2) {
-                if (j >= S - a.H)
-                    hout[j - S + a.H] = mk<T>((s1[2 * e] + c1[2 * e]) * sc, (s1[2 * e + 1] + c1[2 * e + 1]) * sc);
+                if (j >= S - a.H) hout[j - S + a.H] = o1;
             }
         } else {
-            if (j < a.Ls) hout[j] = y0;
+            if (j < a.Ls) hout[j] = o0;
         }
     }
 }

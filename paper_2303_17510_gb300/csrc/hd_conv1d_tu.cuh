@@ -1,18 +1,35 @@
 // hd_conv1d_tu.cuh -- instantiation table of the fused 1D kernels for one
 // (dtype, kind) pair.  Included by the hd_conv1d_<dtype>_<kind>.cu files with
-// HD_REAL, HD_KIND, HD_DT and HD_KN defined.
+// HD_REAL, HD_KIND, HD_DT, HD_KN and HD_SE_EXTRA defined.
 #include "hd_dispatch.h"
 
 namespace hd {
 
 namespace {
 
-template <class R, int S, int E, int KIND, int MULT, int NB>
+template <class R, int S, int E, int MULT>
+size_t group_smem(int ls_pad) {
+    constexpr int A = MULT == MULT_PRODUCT ? 2 : 3;
+    return size_t(A) * (size_t(ls_pad) + FftShape<S, E>::SMEM) * sizeof(cplx<R>);
+}
+
+template <class R, int S, int E, int MULT>
+int groups_for(int ls_pad) {
+    const int T = S / E;
+    int G = 256 / T;
+    if (G < 1) G = 1;
+    const size_t per = group_smem<R, S, E, MULT>(ls_pad);
+    while (G > 1 && per * G > kMaxSmemPerBlock) --G;
+    return per > kMaxSmemPerBlock ? 0 : G;
+}
+
+template <class R, int S, int E, int KIND, int MULT, int NB, bool COMP, int MINB>
 cudaError_t launch_one(const ConvArgs& a, cudaStream_t st) {
     constexpr int T = S / E;
-    constexpr int G = (256 / T) < 1 ? 1 : (256 / T);
-    const size_t smem = size_t(G) * FftShape<S, E>::SMEM * sizeof(cplx<R>);
-    auto k = conv1d_kernel<R, S, E, KIND, MULT, NB, G>;
+    const int G = groups_for<R, S, E, MULT>(a.ls_pad);
+    if (G < 1) return cudaErrorInvalidValue;
+    const size_t smem = size_t(G) * group_smem<R, S, E, MULT>(a.ls_pad);
+    auto k = conv1d_kernel<R, S, E, KIND, MULT, NB, COMP, MINB>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -35,65 +52,72 @@ cudaError_t launch_fwd(const ConvArgs& a, int r, int m, void* out, cudaStream_t 
     return cudaGetLastError();
 }
 
-}  // namespace
-
-// (S, E) pairs compiled for this dtype: every power of two up to HD_SMAX with
-// E = 8 (E = S below 8), plus E = 16 where registers allow (one folded block,
-// product mult, FP32).
-#define HD_SE_LIST(X)                                                                                        \
-    X(2, 2) X(4, 4) X(8, 8) X(16, 8) X(32, 8) X(64, 8) X(128, 8) X(256, 8) X(512, 8) X(1024, 8) X(2048, 8)   \
-    HD_SE_EXTRA(X)
-
-// Combinations that get a kernel: Hermitian data folds into one output block,
-// centered data into two; E = 16 keeps 2E accumulators plus three spectra in
-// registers only for one block and the binary product.
-template <int E, int MULT, int NB>
+// Hermitian data folds into one output block, centered data into two;
+// compensated accumulation is an FP32 option.
+template <int MULT, int NB, bool COMP>
 constexpr bool combo_ok() {
     return !((HD_KIND == KIND_HERMITIAN && NB != 1) || (HD_KIND == KIND_CENTERED && NB != 2) ||
-             (E == 16 && (NB != 1 || MULT != MULT_PRODUCT)));
+             (sizeof(HD_REAL) == 8 && COMP));
 }
 
-template <int S, int E, int MULT, int NB>
+template <int S, int E, int MINB, int MULT, int NB, bool COMP>
 cudaError_t pick(const ConvArgs& a, cudaStream_t st) {
-    if constexpr (combo_ok<E, MULT, NB>()) return launch_one<HD_REAL, S, E, HD_KIND, MULT, NB>(a, st);
+    if constexpr (combo_ok<MULT, NB, COMP>()) return launch_one<HD_REAL, S, E, HD_KIND, MULT, NB, COMP, MINB>(a, st);
     else return cudaErrorInvalidValue;
 }
 
-#define HD_NBMULT_CASES(SS, EE)                                                                                \
-    if (c.S == SS && c.E == EE) {                                                                              \
-        if (c.mult == MULT_PRODUCT && c.nb == 1) return pick<SS, EE, MULT_PRODUCT, 1>(a, st);                  \
-        if (c.mult == MULT_PAIRS3 && c.nb == 1) return pick<SS, EE, MULT_PAIRS3, 1>(a, st);                    \
-        if (c.mult == MULT_PRODUCT && c.nb == 2) return pick<SS, EE, MULT_PRODUCT, 2>(a, st);                  \
-        if (c.mult == MULT_PAIRS3 && c.nb == 2) return pick<SS, EE, MULT_PAIRS3, 2>(a, st);                    \
+template <int S, int E, int MINB, int MULT, int NB, bool COMP>
+bool fits(int ls_pad) {
+    if constexpr (combo_ok<MULT, NB, COMP>()) return groups_for<HD_REAL, S, E, MULT>(ls_pad) >= 1;
+    else return false;
+}
+
+}  // namespace
+
+// Kernel variants compiled for this dtype, as (S, E, MINB): HD_VARIANTS is
+// defined by the including unit.
+#define HD_COMBOS(SS, EE, MB, FN, ...)                                                                       \
+    if (c.S == SS && c.E == EE && c.minb == MB) {                                                            \
+        if (c.mult == MULT_PRODUCT && c.nb == 1 && !c.comp) return FN<SS, EE, MB, MULT_PRODUCT, 1, false>(__VA_ARGS__); \
+        if (c.mult == MULT_PRODUCT && c.nb == 1 && c.comp) return FN<SS, EE, MB, MULT_PRODUCT, 1, true>(__VA_ARGS__);   \
+        if (c.mult == MULT_PAIRS3 && c.nb == 1 && !c.comp) return FN<SS, EE, MB, MULT_PAIRS3, 1, false>(__VA_ARGS__);   \
+        if (c.mult == MULT_PAIRS3 && c.nb == 1 && c.comp) return FN<SS, EE, MB, MULT_PAIRS3, 1, true>(__VA_ARGS__);     \
+        if (c.mult == MULT_PRODUCT && c.nb == 2 && !c.comp) return FN<SS, EE, MB, MULT_PRODUCT, 2, false>(__VA_ARGS__); \
+        if (c.mult == MULT_PRODUCT && c.nb == 2 && c.comp) return FN<SS, EE, MB, MULT_PRODUCT, 2, true>(__VA_ARGS__);   \
+        if (c.mult == MULT_PAIRS3 && c.nb == 2 && !c.comp) return FN<SS, EE, MB, MULT_PAIRS3, 2, false>(__VA_ARGS__);   \
+        if (c.mult == MULT_PAIRS3 && c.nb == 2 && c.comp) return FN<SS, EE, MB, MULT_PAIRS3, 2, true>(__VA_ARGS__);     \
     }
 
-#define HD_AVAIL_CASE(SS, EE)                                                                                  \
-    if (c.S == SS && c.E == EE) {                                                                              \
-        if (c.mult == MULT_PRODUCT && c.nb == 1) return combo_ok<EE, MULT_PRODUCT, 1>();                      \
-        if (c.mult == MULT_PAIRS3 && c.nb == 1) return combo_ok<EE, MULT_PAIRS3, 1>();                        \
-        if (c.mult == MULT_PRODUCT && c.nb == 2) return combo_ok<EE, MULT_PRODUCT, 2>();                      \
-        if (c.mult == MULT_PAIRS3 && c.nb == 2) return combo_ok<EE, MULT_PAIRS3, 2>();                        \
-        return false;                                                                                        \
-    }
-#define HD_FWD_CASE(SS, EE) if (c.S == SS && c.E == EE) return launch_fwd<HD_REAL, SS, EE, HD_KIND>(a, r, m, out, st);
+#define HD_LAUNCH_CASE(SS, EE, MB) HD_COMBOS(SS, EE, MB, pick, a, st)
+#define HD_AVAIL_CASE(SS, EE, MB) HD_COMBOS(SS, EE, MB, fits, ls_pad)
+#define HD_FWD_CASE(SS, EE, MB) \
+    if (c.S == SS && c.E == EE) return launch_fwd<HD_REAL, SS, EE, HD_KIND>(a, r, m, out, st);
+#define HD_LIST_CASE(SS, EE, MB) \
+    if (n < cap) { out[n].S = SS; out[n].E = EE; out[n].minb = MB; } ++n;
 
 #define HD_CAT2(a, b, c, d) a##b##c##d
 #define HD_FN(base, DT, KN) HD_CAT2(base, DT, _, KN)
 
-bool HD_FN(conv1d_available_, HD_DT, HD_KN)(const Conv1dCfg& c) {
-    HD_SE_LIST(HD_AVAIL_CASE)
+bool HD_FN(conv1d_available_, HD_DT, HD_KN)(const Conv1dCfg& c, int ls_pad) {
+    HD_VARIANTS(HD_AVAIL_CASE)
     return false;
 }
 
 cudaError_t HD_FN(conv1d_launch_, HD_DT, HD_KN)(const Conv1dCfg& c, const ConvArgs& a, cudaStream_t st) {
-    HD_SE_LIST(HD_NBMULT_CASES)
+    HD_VARIANTS(HD_LAUNCH_CASE)
     return cudaErrorInvalidValue;
 }
 
 cudaError_t HD_FN(forward_residue_launch_, HD_DT, HD_KN)(const Conv1dCfg& c, const ConvArgs& a, int r, int m,
                                                          void* out, cudaStream_t st) {
-    HD_SE_LIST(HD_FWD_CASE)
+    HD_VARIANTS(HD_FWD_CASE)
     return cudaErrorInvalidValue;
+}
+
+int HD_FN(conv1d_variants_, HD_DT, HD_KN)(Conv1dCfg* out, int cap) {
+    int n = 0;
+    HD_VARIANTS(HD_LIST_CASE)
+    return n;
 }
 
 }  // namespace hd

@@ -14,28 +14,30 @@ struct Conv1dCfg {
     int nb;      // folded blocks: 1 or 2
     int S;       // transform size (power of two)
     int E;       // values per thread
+    bool comp;   // compensated (TwoSum) accumulation of residue contributions
+    int minb;    // CTAs per SM the register allocation allows (1 or 2)
 };
 
-// Groups (convolutions) per CTA for a transform of size S with E values per thread.
-inline int conv1d_groups(int S, int E) {
-    int T = S / E;
-    int G = 256 / T;
-    return G < 1 ? 1 : G;
-}
+// dynamic shared memory limit of one CTA on sm_103a
+constexpr size_t kMaxSmemPerBlock = 227 * 1024;
 
-// true when a kernel instance exists for cfg
-bool conv1d_available(const Conv1dCfg& c);
+// true when a kernel instance exists for cfg and its shared memory fits for
+// staged rows of ls_pad values
+bool conv1d_available(const Conv1dCfg& c, int ls_pad);
 // launch `count` convolutions (a.count) of cfg on stream
 cudaError_t conv1d_launch(const Conv1dCfg& c, const ConvArgs& a, cudaStream_t st);
+// compiled (S, E, minb) variants for cfg's dtype and kind; returns the count
+int conv1d_variants(int dtype, int kind, Conv1dCfg* out, int cap);
 // forward transform of residue r of one input (debug path)
 cudaError_t forward_residue_launch(const Conv1dCfg& c, const ConvArgs& a, int r, int m, void* out, cudaStream_t st);
 
 // per translation unit entry points (dtype x kind)
 #define HD_DECL_TU(DT, KN)                                                                                   \
-    bool conv1d_available_##DT##_##KN(const Conv1dCfg& c);                                                    \
+    bool conv1d_available_##DT##_##KN(const Conv1dCfg& c, int ls_pad);                                                    \
     cudaError_t conv1d_launch_##DT##_##KN(const Conv1dCfg& c, const ConvArgs& a, cudaStream_t st);            \
     cudaError_t forward_residue_launch_##DT##_##KN(const Conv1dCfg& c, const ConvArgs& a, int r, int m,       \
-                                                    void* out, cudaStream_t st);
+                                                    void* out, cudaStream_t st);                              \
+    int conv1d_variants_##DT##_##KN(Conv1dCfg* out, int cap);
 HD_DECL_TU(f32, complex)
 HD_DECL_TU(f32, centered)
 HD_DECL_TU(f32, hermitian)

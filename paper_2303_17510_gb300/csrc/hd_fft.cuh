@@ -239,8 +239,12 @@ __device__ __forceinline__ T ldtw(const T* p) {
     return __ldg(p);
 }
 
-// Forward pass k: radix-R DFT then twiddle zeta_{N_k}^{c k1}.
-template <int S, int E, int k, bool INV, class T>
+// Pass k on NA independent arrays held back to back in v (array a in
+// v[a*E .. a*E+E)): radix-R DFT, then the twiddle zeta_{N_k}^{c k1} (forward);
+// the inverse applies the conjugate twiddle first, then the inverse DFT.  The
+// twiddles depend only on the thread's position and are loaded once for all
+// arrays.
+template <int S, int E, int k, bool INV, int NA, class T>
 __device__ __forceinline__ void fft_pass(T* v, const T* __restrict__ twS, int tau) {
     using Sh = FftShape<S, E>;
     constexpr int R = Sh::radix(k);
@@ -249,30 +253,35 @@ __device__ __forceinline__ void fft_pass(T* v, const T* __restrict__ twS, int ta
     constexpr int STR = S / N;
 #pragma unroll
     for (int beta = 0; beta < E / R; ++beta) {
-        T* x = v + beta * R;
         const int nu = tau + Sh::T * beta;
         const int c = nu & (Q - 1);
         if constexpr (!INV) {
-            dft_reg<R, false>(x);
-            if constexpr (Q > 1) {
 #pragma unroll
-                for (int k1 = 1; k1 < R; ++k1) x[k1] = cmul(x[k1], ldtw(twS + c * k1 * STR));
-            }
-        } else {
-            if constexpr (Q > 1) {
+            for (int a = 0; a < NA; ++a) dft_reg<R, false>(v + a * E + beta * R);
+        }
+        if constexpr (Q > 1) {
 #pragma unroll
-                for (int k1 = 1; k1 < R; ++k1) x[k1] = cmulc(x[k1], ldtw(twS + c * k1 * STR));
+            for (int k1 = 1; k1 < R; ++k1) {
+                const T w = ldtw(twS + c * k1 * STR);
+#pragma unroll
+                for (int a = 0; a < NA; ++a) {
+                    T& x = v[a * E + beta * R + k1];
+                    x = INV ? cmulc(x, w) : cmul(x, w);
+                }
             }
-            dft_reg<R, true>(x);
+        }
+        if constexpr (INV) {
+#pragma unroll
+            for (int a = 0; a < NA; ++a) dft_reg<R, true>(v + a * E + beta * R);
         }
     }
 }
 
-// Exchange between pass k and pass k+1.  FWD: from the layout after pass k
-// to the layout pass k+1 reads; otherwise the reverse.  `sm` is the group's
-// padded buffer.  Two barriers: after the writes, and before the buffer is
-// written again.
-template <int S, int E, int k, bool FWD, class T>
+// Exchange between pass k and pass k+1 for NA arrays (array a uses the padded
+// buffer sm + a * SMEM).  FWD: from the layout after pass k to the layout pass
+// k+1 reads; otherwise the reverse.  Two barriers: after the writes, and
+// before the buffers are written again.
+template <int S, int E, int k, bool FWD, int NA, class T>
 __device__ __forceinline__ void fft_exchange(T* v, T* sm, int tau) {
     using Sh = FftShape<S, E>;
     constexpr int R = Sh::radix(k);
@@ -284,7 +293,9 @@ __device__ __forceinline__ void fft_exchange(T* v, T* sm, int tau) {
         for (int beta = 0; beta < E / R; ++beta) {
             const int nu = tau + Sh::T * beta;
 #pragma unroll
-            for (int k1 = 0; k1 < R; ++k1) sm[padidx(nu + V * k1)] = v[beta * R + k1];
+            for (int k1 = 0; k1 < R; ++k1)
+#pragma unroll
+                for (int a = 0; a < NA; ++a) sm[a * Sh::SMEM + padidx(nu + V * k1)] = v[a * E + beta * R + k1];
         }
         __syncthreads();
 #pragma unroll
@@ -292,7 +303,10 @@ __device__ __forceinline__ void fft_exchange(T* v, T* sm, int tau) {
             const int nu = tau + Sh::T * beta;
             const int b = nu / Qn, c = nu & (Qn - 1);
 #pragma unroll
-            for (int i = 0; i < Rn; ++i) v[beta * Rn + i] = sm[padidx(b * Rn * Qn + i * Qn + c)];
+            for (int i = 0; i < Rn; ++i)
+#pragma unroll
+                for (int a = 0; a < NA; ++a)
+                    v[a * E + beta * Rn + i] = sm[a * Sh::SMEM + padidx(b * Rn * Qn + i * Qn + c)];
         }
         __syncthreads();
     } else {
@@ -301,48 +315,53 @@ __device__ __forceinline__ void fft_exchange(T* v, T* sm, int tau) {
             const int nu = tau + Sh::T * beta;
             const int b = nu / Qn, c = nu & (Qn - 1);
 #pragma unroll
-            for (int i = 0; i < Rn; ++i) sm[padidx(b * Rn * Qn + i * Qn + c)] = v[beta * Rn + i];
+            for (int i = 0; i < Rn; ++i)
+#pragma unroll
+                for (int a = 0; a < NA; ++a)
+                    sm[a * Sh::SMEM + padidx(b * Rn * Qn + i * Qn + c)] = v[a * E + beta * Rn + i];
         }
         __syncthreads();
 #pragma unroll
         for (int beta = 0; beta < E / R; ++beta) {
             const int nu = tau + Sh::T * beta;
 #pragma unroll
-            for (int k1 = 0; k1 < R; ++k1) v[beta * R + k1] = sm[padidx(nu + V * k1)];
+            for (int k1 = 0; k1 < R; ++k1)
+#pragma unroll
+                for (int a = 0; a < NA; ++a) v[a * E + beta * R + k1] = sm[a * Sh::SMEM + padidx(nu + V * k1)];
         }
         __syncthreads();
     }
 }
 
-template <int S, int E, int k, class T>
+template <int S, int E, int k, int NA, class T>
 __device__ __forceinline__ void fft_fwd_from(T* v, T* sm, const T* __restrict__ twS, int tau) {
     using Sh = FftShape<S, E>;
-    fft_pass<S, E, k, false>(v, twS, tau);
+    fft_pass<S, E, k, false, NA>(v, twS, tau);
     if constexpr (k + 1 < Sh::K) {
-        fft_exchange<S, E, k, true>(v, sm, tau);
-        fft_fwd_from<S, E, k + 1>(v, sm, twS, tau);
+        fft_exchange<S, E, k, true, NA>(v, sm, tau);
+        fft_fwd_from<S, E, k + 1, NA>(v, sm, twS, tau);
     }
 }
 
-template <int S, int E, int k, class T>
+template <int S, int E, int k, int NA, class T>
 __device__ __forceinline__ void fft_inv_from(T* v, T* sm, const T* __restrict__ twS, int tau) {
-    fft_pass<S, E, k, true>(v, twS, tau);
+    fft_pass<S, E, k, true, NA>(v, twS, tau);
     if constexpr (k > 0) {
-        fft_exchange<S, E, k - 1, false>(v, sm, tau);
-        fft_inv_from<S, E, k - 1>(v, sm, twS, tau);
+        fft_exchange<S, E, k - 1, false, NA>(v, sm, tau);
+        fft_inv_from<S, E, k - 1, NA>(v, sm, twS, tau);
     }
 }
 
-// Forward FFT: natural layout in, spectral layout out.
-template <int S, int E, class T>
+// Forward FFT of NA arrays: natural layout in, spectral layout out.
+template <int S, int E, int NA = 1, class T>
 __device__ __forceinline__ void fft_forward(T* v, T* sm, const T* __restrict__ twS, int tau) {
-    fft_fwd_from<S, E, 0>(v, sm, twS, tau);
+    fft_fwd_from<S, E, 0, NA>(v, sm, twS, tau);
 }
 
-// Inverse FFT (unnormalized): spectral layout in, natural layout out.
-template <int S, int E, class T>
+// Inverse FFT (unnormalized) of NA arrays: spectral layout in, natural layout out.
+template <int S, int E, int NA = 1, class T>
 __device__ __forceinline__ void fft_inverse(T* v, T* sm, const T* __restrict__ twS, int tau) {
-    fft_inv_from<S, E, FftShape<S, E>::K - 1>(v, sm, twS, tau);
+    fft_inv_from<S, E, FftShape<S, E>::K - 1, NA>(v, sm, twS, tau);
 }
 
 // Frequency index held by register e of thread tau in the spectral layout.

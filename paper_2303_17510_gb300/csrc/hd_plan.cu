@@ -2,12 +2,19 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
 #include "hd_plan.h"
 
 namespace hd {
+
+// FP32 residue sums are compensated unless HD_COMP=0 is set in the environment.
+bool comp_default() {
+    const char* e = std::getenv("HD_COMP");
+    return !(e && e[0] == '0');
+}
 
 namespace {
 
@@ -71,7 +78,9 @@ hd_status fill_axis(int dtype, int kind, int mult, int64_t L, int64_t M, int64_t
     ax->D = D <= 0 ? 1 : D;
     ax->nb = nb;
     ax->E = S < 8 ? (int)S : 8;
-    if (fused_supported(dtype, kind, mult, S, nb)) {
+    ax->comp = dtype == HD_F32 && comp_default();
+    ax->minb = default_minb(dtype, S);
+    if (fused_supported(dtype, kind, mult, S, nb, ax->Ls, ax->comp, ax->E, ax->minb)) {
         ax->path = PATH_FUSED;
         return HD_OK;
     }
@@ -109,7 +118,9 @@ hd_status choose_axis(int dtype, int kind, int mult, int A, int B, int64_t L, in
     return found ? HD_OK : HD_ERR_UNSUPPORTED;
 }
 
-hd_status plan_create(hd_plan** out, const hd_desc* d) {
+namespace {
+
+hd_status check_desc_1d(const hd_desc* d) {
     if (d->ndim != 1) return HD_ERR_UNSUPPORTED;
     if (d->kind < HD_COMPLEX || d->kind > HD_HERMITIAN) return HD_ERR_INVALID;
     if (d->dtype != HD_F32 && d->dtype != HD_F64) return HD_ERR_INVALID;
@@ -117,9 +128,12 @@ hd_status plan_create(hd_plan** out, const hd_desc* d) {
     if (!((d->mult == HD_MULT_PRODUCT && d->A == 2) || (d->mult == HD_MULT_SUM_PAIRS3 && d->A == 3)))
         return HD_ERR_INVALID;
     if (d->L[0] <= 0 || d->M[0] <= 0 || d->m[0] < 0 || d->p[0] < 0 || d->q[0] < 0) return HD_ERR_INVALID;
-    const int64_t bound = hd_dealias_bound(d->kind, d->mult, d->L[0]);
-    if (d->M[0] < bound) return HD_ERR_ALIASED;
+    if (d->M[0] < hd_dealias_bound(d->kind, d->mult, d->L[0])) return HD_ERR_ALIASED;
+    return HD_OK;
+}
 
+// Allocates the plan for a filled axis and uploads its twiddle tables.
+hd_status plan_finish(const hd_desc* d, const AxisPlan& ax, hd_plan** out) {
     hd_plan* pl = new (std::nothrow) hd_plan;
     if (!pl) return HD_ERR_NOMEM;
     std::memset(pl, 0, sizeof(*pl));
@@ -130,29 +144,55 @@ hd_status plan_create(hd_plan** out, const hd_desc* d) {
     pl->A = d->A;
     pl->B = d->B;
     pl->sticky = HD_OK;
+    pl->ax[0] = ax;
+    pl->ax[0].twS = pl->ax[0].twN = nullptr;
     if (cudaGetDevice(&pl->device) != cudaSuccess) {
         cudaGetLastError();
         delete pl;
         return HD_ERR_CUDA;
     }
-    AxisPlan& ax = pl->ax[0];
-    hd_status st;
-    if (d->m[0] == 0) st = choose_axis(d->dtype, d->kind, d->mult, d->A, d->B, d->L[0], d->M[0], &ax);
-    else st = fill_axis(d->dtype, d->kind, d->mult, d->L[0], d->M[0], d->m[0], d->p[0], d->q[0], d->D[0], &ax);
-    if (st != HD_OK) {
-        delete pl;
-        return st;
-    }
-    if (d->D[0] > 0) ax.D = d->D[0];
     pl->instance_elems = ax.Ls;
-    st = upload_table(ax.S, d->dtype, &ax.twS);
-    if (st == HD_OK) st = upload_table(ax.S * ax.n, d->dtype, &ax.twN);
+    hd_status st = upload_table(ax.S, d->dtype, &pl->ax[0].twS);
+    if (st == HD_OK) st = upload_table(ax.S * ax.n, d->dtype, &pl->ax[0].twN);
     if (st != HD_OK) {
         plan_free(pl);
         return st;
     }
     *out = pl;
     return HD_OK;
+}
+
+}  // namespace
+
+hd_status plan_create_from(hd_plan** out, const hd_desc* d, const hd_candidate* c) {
+    hd_status st = check_desc_1d(d);
+    if (st != HD_OK) return st;
+    AxisPlan ax;
+    st = fill_axis(d->dtype, d->kind, d->mult, d->L[0], d->M[0], c->m, c->p, c->q, c->D, &ax);
+    if (st != HD_OK && st != HD_ERR_UNSUPPORTED) return st;
+    if (ax.S != c->S || ax.n != c->n) return HD_ERR_INVALID;
+    ax.E = c->E;
+    ax.minb = c->minb;
+    ax.comp = c->comp != 0 && d->dtype == HD_F32;
+    if (!fused_supported(d->dtype, d->kind, d->mult, ax.S, ax.nb, ax.Ls, ax.comp, ax.E, ax.minb))
+        return HD_ERR_UNSUPPORTED;
+    ax.path = PATH_FUSED;
+    return plan_finish(d, ax, out);
+}
+
+hd_status plan_create(hd_plan** out, const hd_desc* d) {
+    hd_status st = check_desc_1d(d);
+    if (st != HD_OK) return st;
+    if (d->m[0] == 0) {
+        hd_candidate c;
+        if (cache_lookup(d, &c) && plan_create_from(out, d, &c) == HD_OK) return HD_OK;
+    }
+    AxisPlan ax;
+    if (d->m[0] == 0) st = choose_axis(d->dtype, d->kind, d->mult, d->A, d->B, d->L[0], d->M[0], &ax);
+    else st = fill_axis(d->dtype, d->kind, d->mult, d->L[0], d->M[0], d->m[0], d->p[0], d->q[0], d->D[0], &ax);
+    if (st != HD_OK) return st;
+    if (d->D[0] > 0) ax.D = d->D[0];
+    return plan_finish(d, ax, out);
 }
 
 ConvArgs make_conv_args(const hd_plan& pl, const AxisPlan& ax, int64_t count, const void* const* f, void* const* h,
@@ -168,6 +208,7 @@ ConvArgs make_conv_args(const hd_plan& pl, const AxisPlan& ax, int64_t count, co
     a.H = (int)(ax.L / 2);
     a.n = (int)ax.n;
     a.N = (int)(ax.n * ax.S);
+    a.ls_pad = (int)staged_row(ax.Ls);
     a.twS = ax.twS;
     a.twN = ax.twN;
     a.invN = 1.0 / (double)(ax.n * ax.S);
@@ -182,6 +223,8 @@ Conv1dCfg fused_cfg(const hd_plan& pl, const AxisPlan& ax) {
     c.nb = ax.nb;
     c.S = (int)ax.S;
     c.E = ax.E;
+    c.comp = ax.comp;
+    c.minb = ax.minb;
     return c;
 }
 

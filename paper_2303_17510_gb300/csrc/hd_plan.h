@@ -5,6 +5,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 
 #include "../../include/hd.h"
 #include "hd_dispatch.h"
@@ -24,6 +25,8 @@ struct AxisPlan {
     int D;
     int nb;
     int E;
+    bool comp;         // compensated residue accumulation (FP32)
+    int minb;          // kernel variant: CTAs per SM of the register allocation
     int path;
     void* twS;         // zeta_S^k, k < S (device)
     void* twN;         // zeta_N^k, k < N = n S (device)
@@ -37,7 +40,10 @@ int max_fused_S(int dtype);
 void axis_geometry(int kind, int64_t L, int64_t m, int64_t p, int64_t q, int64_t* S, int64_t* n, int* nb);
 hd_status validate_axis(int kind, int mult, int64_t L, int64_t M, int64_t m, int64_t p, int64_t q, int64_t* S,
                         int64_t* n, int* nb);
-bool fused_supported(int dtype, int kind, int mult, int64_t S, int nb);
+bool fused_supported(int dtype, int kind, int mult, int64_t S, int nb, int64_t Ls, bool comp, int E, int minb);
+int default_minb(int dtype, int64_t S);
+// staged row length in shared memory for Ls stored values (even: 16-byte rows)
+inline int64_t staged_row(int64_t Ls) { return (Ls + 1) & ~int64_t(1); }
 double cost_model(int kind, int A, int B, int64_t S, int64_t n);
 
 }  // namespace hd
@@ -65,6 +71,14 @@ void plan_free(hd_plan* plan);
 ConvArgs make_conv_args(const hd_plan& pl, const AxisPlan& ax, int64_t count, const void* const* f,
                         void* const* h, int64_t stride);
 Conv1dCfg fused_cfg(const hd_plan& pl, const AxisPlan& ax);
+
+// Plan for an explicit candidate (kernel variant included).
+hd_status plan_create_from(hd_plan** out, const hd_desc* d, const hd_candidate* c);
+bool comp_default();
+// legal, supported candidates of a 1D description (see hd_enumerate_candidates)
+int enumerate_candidates(const hd_desc* d, std::vector<hd_candidate>* out);
+// tuned candidate recorded for the description, if any
+bool cache_lookup(const hd_desc* d, hd_candidate* c);
 
 // Legal, supported (m, p, q) of one axis chosen by the cost model; fills ax.
 hd_status choose_axis(int dtype, int kind, int mult, int A, int B, int64_t L, int64_t M, AxisPlan* ax);

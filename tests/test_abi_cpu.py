@@ -67,3 +67,28 @@ def test_invalid_arguments(hd):
     assert hd.dealias_bound("complex", 0) == -1
     assert hd.lib.hd_status_string(6).decode().startswith("HD_ERR_ALIASED")
     assert hd.lib.hd_plan_destroy(None) == 0
+
+
+@pytest.mark.parametrize("kind", ["complex", "centered", "hermitian"])
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_enumerated_candidates_are_legal(hd, kind, dtype):
+    for L in (1, 7, 100, 1024, 4096):
+        for M in (params.dealias_bound(kind, L), 3 * L):
+            cands = hd.enumerate_candidates(L=L, M=M, kind=kind, dtype=dtype)
+            assert cands, (kind, L, M)
+            seen = set()
+            for c in cands:
+                m, p, q, S, n = c["m"], c["p"], c["q"], c["S"], c["n"]
+                assert q * m >= M and S * n == q * m
+                if (p, q) != (1, 1):
+                    want = params.derive(kind, L, M, m)
+                    # the paper's p, or explicit padding to a power-of-two multiple
+                    assert p == want[0] or (p > want[0] and p & (p - 1) == 0)
+                else:
+                    assert m >= M
+                key = (S, n, c["E"], c["minb"])
+                assert key not in seen
+                seen.add(key)
+            # at least one candidate with the paper's own p for the largest legal m
+    with pytest.raises(hd.HdError):
+        hd.enumerate_candidates(L=0, M=5)

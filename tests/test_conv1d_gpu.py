@@ -155,7 +155,7 @@ def test_edge_cases_and_errors(hd):
     import torch
     # L = 1: the product of two scalars
     f = make_inputs("complex", 1, 2, 1, 9)
-    with hd.Plan(1, 1, m=1) as plan:
+    with hd.Plan(1, 1) as plan:
         got = run_conv(hd, plan, f)
         assert rel_l2(got, f[0] * f[1]) < 1e-6
     # count = 0 is a no-op
