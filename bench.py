@@ -149,7 +149,10 @@ def main():
     ap.add_argument("--impl", default="hd", choices=["hd", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--m", type=str, default="auto", help="override m per sub-config, e.g. 2048,4096")
+    ap.add_argument("--count", type=int, default=4096, help="batch size per sub-config (profiling cases)")
     args = ap.parse_args()
+    global COUNT
+    COUNT = args.count
     if args.impl == "reference":
         run_reference(args)
         return
