@@ -239,13 +239,34 @@ __device__ __forceinline__ T ldtw(const T* p) {
     return __ldg(p);
 }
 
+// Twiddle sources for the FFT passes: tw(k) = zeta_S^k, 0 <= k < S.
+// TwGlobal reads the full table through the read-only cache; TwShared reads a
+// half table held in shared memory (zeta_S^{k + S/2} = -zeta_S^k).
+template <class T>
+struct TwGlobal {
+    const T* __restrict__ p;
+    __device__ __forceinline__ T operator()(int k) const { return __ldg(p + k); }
+};
+template <class T, int S>
+struct TwShared {
+    const T* p;   // zeta_S^k, k < S/2
+    __device__ __forceinline__ T operator()(int k) const {
+        if constexpr (S < 2) {
+            return p[0];
+        } else {
+            const T w = p[k & (S / 2 - 1)];
+            return (k & (S / 2)) ? mk<T>(-w.x, -w.y) : w;
+        }
+    }
+};
+
 // Pass k on NA independent arrays held back to back in v (array a in
 // v[a*E .. a*E+E)): radix-R DFT, then the twiddle zeta_{N_k}^{c k1} (forward);
 // the inverse applies the conjugate twiddle first, then the inverse DFT.  The
 // twiddles depend only on the thread's position and are loaded once for all
 // arrays.
-template <int S, int E, int k, bool INV, int NA, class T>
-__device__ __forceinline__ void fft_pass(T* v, const T* __restrict__ twS, int tau) {
+template <int S, int E, int k, bool INV, int NA, class T, class TW>
+__device__ __forceinline__ void fft_pass(T* v, const TW& tw, int tau) {
     using Sh = FftShape<S, E>;
     constexpr int R = Sh::radix(k);
     constexpr int N = Sh::sub(k);
@@ -262,7 +283,7 @@ __device__ __forceinline__ void fft_pass(T* v, const T* __restrict__ twS, int ta
         if constexpr (Q > 1) {
 #pragma unroll
             for (int k1 = 1; k1 < R; ++k1) {
-                const T w = ldtw(twS + c * k1 * STR);
+                const T w = tw(c * k1 * STR);
 #pragma unroll
                 for (int a = 0; a < NA; ++a) {
                     T& x = v[a * E + beta * R + k1];
@@ -333,35 +354,35 @@ __device__ __forceinline__ void fft_exchange(T* v, T* sm, int tau) {
     }
 }
 
-template <int S, int E, int k, int NA, class T>
-__device__ __forceinline__ void fft_fwd_from(T* v, T* sm, const T* __restrict__ twS, int tau) {
+template <int S, int E, int k, int NA, class T, class TW>
+__device__ __forceinline__ void fft_fwd_from(T* v, T* sm, const TW& tw, int tau) {
     using Sh = FftShape<S, E>;
-    fft_pass<S, E, k, false, NA>(v, twS, tau);
+    fft_pass<S, E, k, false, NA>(v, tw, tau);
     if constexpr (k + 1 < Sh::K) {
         fft_exchange<S, E, k, true, NA>(v, sm, tau);
-        fft_fwd_from<S, E, k + 1, NA>(v, sm, twS, tau);
+        fft_fwd_from<S, E, k + 1, NA>(v, sm, tw, tau);
     }
 }
 
-template <int S, int E, int k, int NA, class T>
-__device__ __forceinline__ void fft_inv_from(T* v, T* sm, const T* __restrict__ twS, int tau) {
-    fft_pass<S, E, k, true, NA>(v, twS, tau);
+template <int S, int E, int k, int NA, class T, class TW>
+__device__ __forceinline__ void fft_inv_from(T* v, T* sm, const TW& tw, int tau) {
+    fft_pass<S, E, k, true, NA>(v, tw, tau);
     if constexpr (k > 0) {
         fft_exchange<S, E, k - 1, false, NA>(v, sm, tau);
-        fft_inv_from<S, E, k - 1, NA>(v, sm, twS, tau);
+        fft_inv_from<S, E, k - 1, NA>(v, sm, tw, tau);
     }
 }
 
 // Forward FFT of NA arrays: natural layout in, spectral layout out.
-template <int S, int E, int NA = 1, class T>
-__device__ __forceinline__ void fft_forward(T* v, T* sm, const T* __restrict__ twS, int tau) {
-    fft_fwd_from<S, E, 0, NA>(v, sm, twS, tau);
+template <int S, int E, int NA = 1, class T, class TW>
+__device__ __forceinline__ void fft_forward(T* v, T* sm, const TW& tw, int tau) {
+    fft_fwd_from<S, E, 0, NA>(v, sm, tw, tau);
 }
 
 // Inverse FFT (unnormalized) of NA arrays: spectral layout in, natural layout out.
-template <int S, int E, int NA = 1, class T>
-__device__ __forceinline__ void fft_inverse(T* v, T* sm, const T* __restrict__ twS, int tau) {
-    fft_inv_from<S, E, FftShape<S, E>::K - 1, NA>(v, sm, twS, tau);
+template <int S, int E, int NA = 1, class T, class TW>
+__device__ __forceinline__ void fft_inverse(T* v, T* sm, const TW& tw, int tau) {
+    fft_inv_from<S, E, FftShape<S, E>::K - 1, NA>(v, sm, tw, tau);
 }
 
 // Frequency index held by register e of thread tau in the spectral layout.
