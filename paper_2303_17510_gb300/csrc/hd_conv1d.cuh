@@ -93,13 +93,6 @@ __device__ __forceinline__ void load_fold(const T* f, int j, int S, const ConvAr
     }
 }
 
-// Shared elements of the half twiddle table of a size-S FFT (at least one,
-// keeping the following arrays 16-byte aligned).
-template <int S>
-__host__ __device__ constexpr int tw_half_elems() {
-    return S / 2 < 2 ? 2 : S / 2;
-}
-
 // Block size bound: one group of T threads, or up to 256 threads of groups.
 template <int S, int E>
 struct ConvLaunch {
@@ -108,9 +101,10 @@ struct ConvLaunch {
 };
 
 // One thread group of T = S/E threads per convolution; G = blockDim.x / T
-// groups per CTA.  Shared memory: the half twiddle table zeta_S^k, k < S/2
-// (shared by the groups), then per group the A staged inputs (ls_pad values
-// each) and A padded FFT exchange buffers.
+// groups per CTA.  Shared memory per group: the A staged inputs (ls_pad
+// values each), then A padded FFT exchange buffers.  FFT twiddles are read
+// through the read-only data cache (a shared-memory table measured slower:
+// it competes with the exchanges for shared-memory bandwidth).
 // MINB: CTAs per SM the register allocation must allow (1: up to 255
 // registers for 256 threads; 2: at most 128).
 template <class R, int S, int E, int KIND, int MULT, int NB, bool COMP, int MINB>
@@ -123,14 +117,12 @@ __global__ void __launch_bounds__(ConvLaunch<S, E>::MAXT, MINB) conv1d_kernel(co
     const int G = blockDim.x / TT;
     const int g = threadIdx.x / TT;
     const int tau = threadIdx.x - g * TT;
-    T* twh = reinterpret_cast<T*>(smem_raw);
-    T* st = twh + tw_half_elems<S>() + (size_t)g * (A * a.ls_pad + A * Sh::SMEM);
+    T* st = reinterpret_cast<T*>(smem_raw) + (size_t)g * (A * a.ls_pad + A * Sh::SMEM);
     T* sm = st + A * a.ls_pad;
     const int64_t inst = (int64_t)blockIdx.x * G + g;
     const bool valid = inst < a.count;
     const T* twN = static_cast<const T*>(a.twN);
-    for (int i = threadIdx.x; i < tw_half_elems<S>(); i += blockDim.x) twh[i] = ldtw(static_cast<const T*>(a.twS) + i);
-    const TwShared<T, S> twS{twh};
+    const TwGlobal<T> twS{static_cast<const T*>(a.twS)};
 
     // stage the A inputs of this convolution in shared memory (coalesced)
     if (valid) {

@@ -13,20 +13,14 @@ size_t group_smem(int ls_pad) {
     return size_t(A) * (size_t(ls_pad) + FftShape<S, E>::SMEM) * sizeof(cplx<R>);
 }
 
-template <class R, int S>
-size_t table_smem() {
-    return size_t(tw_half_elems<S>()) * sizeof(cplx<R>);
-}
-
 template <class R, int S, int E, int MULT>
 int groups_for(int ls_pad) {
     const int T = S / E;
     int G = 256 / T;
     if (G < 1) G = 1;
     const size_t per = group_smem<R, S, E, MULT>(ls_pad);
-    const size_t tab = table_smem<R, S>();
-    while (G > 1 && tab + per * G > kMaxSmemPerBlock) --G;
-    return tab + per > kMaxSmemPerBlock ? 0 : G;
+    while (G > 1 && per * G > kMaxSmemPerBlock) --G;
+    return per > kMaxSmemPerBlock ? 0 : G;
 }
 
 template <class R, int S, int E, int KIND, int MULT, int NB, bool COMP, int MINB>
@@ -34,7 +28,7 @@ cudaError_t launch_one(const ConvArgs& a, cudaStream_t st) {
     constexpr int T = S / E;
     const int G = groups_for<R, S, E, MULT>(a.ls_pad);
     if (G < 1) return cudaErrorInvalidValue;
-    const size_t smem = table_smem<R, S>() + size_t(G) * group_smem<R, S, E, MULT>(a.ls_pad);
+    const size_t smem = size_t(G) * group_smem<R, S, E, MULT>(a.ls_pad);
     auto k = conv1d_kernel<R, S, E, KIND, MULT, NB, COMP, MINB>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

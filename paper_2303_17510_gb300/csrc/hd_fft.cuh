@@ -239,25 +239,12 @@ __device__ __forceinline__ T ldtw(const T* p) {
     return __ldg(p);
 }
 
-// Twiddle sources for the FFT passes: tw(k) = zeta_S^k, 0 <= k < S.
-// TwGlobal reads the full table through the read-only cache; TwShared reads a
-// half table held in shared memory (zeta_S^{k + S/2} = -zeta_S^k).
+// Twiddle source for the FFT passes: tw(k) = zeta_S^k, 0 <= k < S, read from
+// the full table through the read-only data cache.
 template <class T>
 struct TwGlobal {
     const T* __restrict__ p;
     __device__ __forceinline__ T operator()(int k) const { return __ldg(p + k); }
-};
-template <class T, int S>
-struct TwShared {
-    const T* p;   // zeta_S^k, k < S/2
-    __device__ __forceinline__ T operator()(int k) const {
-        if constexpr (S < 2) {
-            return p[0];
-        } else {
-            const T w = p[k & (S / 2 - 1)];
-            return (k & (S / 2)) ? mk<T>(-w.x, -w.y) : w;
-        }
-    }
 };
 
 // Pass k on NA independent arrays held back to back in v (array a in
