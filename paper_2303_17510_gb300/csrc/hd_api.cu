@@ -58,14 +58,17 @@ void zeta_fp64(int64_t k, int64_t N, double* c, double* s) {
     *s = y;
 }
 
-hd_status upload_table(int64_t N, int dtype, void** dev) {
+// Uploads (exponent, modulus) pairs as zeta_mod^exp values, generated in FP64
+// and rounded once to the plan's precision.
+hd_status upload_zetas(const std::vector<std::pair<int64_t, int64_t>>& ek, int dtype, void** dev) {
     *dev = nullptr;
+    const int64_t N = (int64_t)ek.size();
     if (N <= 0) return HD_ERR_INVALID;
     const size_t esz = dtype == HD_F64 ? 16 : 8;
     std::vector<unsigned char> host((size_t)N * esz);
     for (int64_t k = 0; k < N; ++k) {
         double c, s;
-        zeta_fp64(k, N, &c, &s);
+        zeta_fp64(ek[k].first, ek[k].second, &c, &s);
         if (dtype == HD_F64) {
             double* p = reinterpret_cast<double*>(host.data()) + 2 * k;
             p[0] = c;
@@ -88,6 +91,41 @@ hd_status upload_table(int64_t N, int dtype, void** dev) {
     }
     *dev = d;
     return HD_OK;
+}
+
+// FFT pass twiddles of a size-S FFT with E values per thread, in the layout
+// of FftShape<S, E>: for each pass k with Q_k = N_k / R_k > 1, entries
+// zeta_{N_k}^{c k1} at (k1 - 1) Q_k + c.
+hd_status upload_fft_twiddles(int64_t S, int E, int dtype, void** dev) {
+    std::vector<std::pair<int64_t, int64_t>> ek;
+    int LS = 0, LE = 0;
+    while ((int64_t(1) << LS) < S) ++LS;
+    while ((1 << LE) < E) ++LE;
+    const int KF = LE > 0 ? LS / LE : 0;
+    const int K = KF + ((LE > 0 && LS % LE) ? 1 : 0);
+    int64_t N = S;
+    for (int k = 0; k < K; ++k) {
+        const int64_t R = k < KF ? E : (int64_t(1) << (LS % LE));
+        const int64_t Q = N / R;
+        if (Q > 1)
+            for (int64_t k1 = 1; k1 < R; ++k1)
+                for (int64_t c = 0; c < Q; ++c) ek.emplace_back(c * k1, N);
+        N = Q;
+    }
+    if (ek.empty()) ek.emplace_back(0, 1);
+    return upload_zetas(ek, dtype, dev);
+}
+
+// Residue twists of an axis with n residues of size S (N = n S):
+// zeta_N^{r j} at r S + j, then zeta_N^{r S} at n S + r.
+hd_status upload_twists(int64_t S, int64_t n, int dtype, void** dev) {
+    const int64_t N = n * S;
+    std::vector<std::pair<int64_t, int64_t>> ek;
+    ek.reserve((size_t)(N + n));
+    for (int64_t r = 0; r < n; ++r)
+        for (int64_t j = 0; j < S; ++j) ek.emplace_back(r * j, N);
+    for (int64_t r = 0; r < n; ++r) ek.emplace_back(r * S, N);
+    return upload_zetas(ek, dtype, dev);
 }
 
 int max_fused_S(int dtype) { return dtype == HD_F64 ? 2048 : 4096; }

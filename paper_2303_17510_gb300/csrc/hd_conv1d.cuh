@@ -51,8 +51,8 @@ struct ConvArgs {
     int n;              // residues
     int N;              // n * S = q * m
     int ls_pad;         // staged row length in shared memory (>= Ls, even)
-    const void* twS;    // zeta_S^k, k < S
-    const void* twN;    // zeta_N^k, k < N
+    const void* twS;    // FFT pass twiddles (FftShape<S, E> layout)
+    const void* twN;    // residue twists: zeta_N^{r j} at r S + j (r < n, j < S), then zeta_N^{r S} at n S + r
     double invN;        // 1 / N
 };
 
@@ -155,13 +155,14 @@ __global__ void __launch_bounds__(ConvLaunch<S, E>::MAXT, MINB) conv1d_kernel(co
 
     if constexpr (KIND != KIND_HERMITIAN) {
         for (int r = 0; r < a.n; ++r) {
-            T cr = ldtw(twN + (int64_t)r * S);          // zeta_N^{r S}
+            const T* twr = twN + (int64_t)r * S;        // zeta_N^{r j}, j < S
+            T cr = ldtw(twN + (int64_t)a.n * S + r);    // zeta_N^{r S}
             if constexpr (KIND == KIND_CENTERED) cr = cconj(cr);
             T v[A * E];
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const int j = tau + TT * e;
-                const T tw = ldtw(twN + r * j);
+                const T tw = ldtw(twr + j);
 #pragma unroll
                 for (int aa = 0; aa < A; ++aa) {
                     T b0, b1;
@@ -183,7 +184,7 @@ __global__ void __launch_bounds__(ConvLaunch<S, E>::MAXT, MINB) conv1d_kernel(co
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const int j = tau + TT * e;
-                const T y = cmulc(p[e], ldtw(twN + r * j));    // zeta_N^{-r j} y_j
+                const T y = cmulc(p[e], ldtw(twr + j));        // zeta_N^{-r j} y_j
                 acc_add<R, COMP>(s0[2 * e], COMP ? c0[2 * e] : dummy, y.x);
                 acc_add<R, COMP>(s0[2 * e + 1], COMP ? c0[2 * e + 1] : dummy, y.y);
                 if constexpr (NB == 2) {
@@ -197,14 +198,16 @@ __global__ void __launch_bounds__(ConvLaunch<S, E>::MAXT, MINB) conv1d_kernel(co
         for (int r1 = 0; r1 < a.n; r1 += 2) {
             const int r2 = r1 + 1;
             const bool has2 = r2 < a.n;
-            const T cr1 = cconj(ldtw(twN + (int64_t)r1 * S));             // zeta_N^{-r1 S}
-            const T cr2 = has2 ? cconj(ldtw(twN + (int64_t)r2 * S)) : czero<T>();
+            const T* twr1 = twN + (int64_t)r1 * S;
+            const T* twr2 = twN + (int64_t)(has2 ? r2 : r1) * S;
+            const T cr1 = cconj(ldtw(twN + (int64_t)a.n * S + r1));      // zeta_N^{-r1 S}
+            const T cr2 = has2 ? cconj(ldtw(twN + (int64_t)a.n * S + r2)) : czero<T>();
             T v[A * E];
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const int j = tau + TT * e;
-                const T t1 = ldtw(twN + r1 * j);
-                const T t2 = has2 ? ldtw(twN + r2 * j) : czero<T>();
+                const T t1 = ldtw(twr1 + j);
+                const T t2 = has2 ? ldtw(twr2 + j) : czero<T>();
 #pragma unroll
                 for (int aa = 0; aa < A; ++aa) {
                     T b0, b1;
@@ -241,8 +244,8 @@ __global__ void __launch_bounds__(ConvLaunch<S, E>::MAXT, MINB) conv1d_kernel(co
                 const T g1 = mk<T>((yj.x + ym.x) * hf, (yj.y - ym.y) * hf);   // (Y_j + conj Y_{S-j}) / 2
                 const T d = mk<T>(yj.x - ym.x, yj.y + ym.y);                  // Y_j - conj Y_{S-j}
                 const T g2 = mk<T>(d.y * hf, -d.x * hf);                       // d / (2i)
-                T y = cmulc(g1, ldtw(twN + r1 * j));
-                if (has2) y = cadd(y, cmulc(g2, ldtw(twN + r2 * j)));
+                T y = cmulc(g1, ldtw(twr1 + j));
+                if (has2) y = cadd(y, cmulc(g2, ldtw(twr2 + j)));
                 acc_add<R, COMP>(s0[2 * e], COMP ? c0[2 * e] : dummy, y.x);
                 acc_add<R, COMP>(s0[2 * e + 1], COMP ? c0[2 * e + 1] : dummy, y.y);
             }
@@ -295,7 +298,7 @@ __global__ void __launch_bounds__(S / E) forward_residue_kernel(const __grid_con
     const TwGlobal<T> twS{static_cast<const T*>(a.twS)};
     const T* twN = static_cast<const T*>(a.twN);
     const T* f = static_cast<const T*>(a.f[0]);
-    T cr = ldtw(twN + (int64_t)r * S);
+    T cr = ldtw(twN + (int64_t)a.n * S + r);
     if constexpr (KIND != KIND_COMPLEX) cr = cconj(cr);
     T v[E];
 #pragma unroll
@@ -303,7 +306,7 @@ __global__ void __launch_bounds__(S / E) forward_residue_kernel(const __grid_con
         const int j = tau + TT * e;
         T b0, b1;
         load_fold<KIND>(f, j, S, a, true, b0, b1);
-        v[e] = cmul(cadd(b0, cmul(cr, b1)), ldtw(twN + r * j));
+        v[e] = cmul(cadd(b0, cmul(cr, b1)), ldtw(twN + (int64_t)r * S + j));
     }
     fft_forward<S, E>(v, sm, twS, tau);
     const int P = S / m;

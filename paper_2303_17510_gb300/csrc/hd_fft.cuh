@@ -230,6 +230,13 @@ struct FftShape {
     static constexpr int RLAST = radix(K - 1);
     // padded shared elements for one transform
     static constexpr int SMEM = S + S / 16;
+    // Twiddle table layout: pass k (with Q_k > 1) stores zeta_{N_k}^{c k1} at
+    // tw_offset(k) + (k1 - 1) Q_k + c, so lanes with consecutive c read
+    // consecutive entries.
+    __host__ __device__ static constexpr int qof(int k) { return sub(k) / radix(k); }
+    __host__ __device__ static constexpr int tw_count(int k) { return qof(k) > 1 ? (radix(k) - 1) * qof(k) : 0; }
+    __host__ __device__ static constexpr int tw_offset(int k) { return k == 0 ? 0 : tw_offset(k - 1) + tw_count(k - 1); }
+    static constexpr int TW_TOTAL = tw_offset(K);
 };
 
 __device__ __forceinline__ int padidx(int a) { return a + (a >> 4); }
@@ -239,12 +246,12 @@ __device__ __forceinline__ T ldtw(const T* p) {
     return __ldg(p);
 }
 
-// Twiddle source for the FFT passes: tw(k) = zeta_S^k, 0 <= k < S, read from
-// the full table through the read-only data cache.
+// Twiddle source for the FFT passes: the per-pass table of FftShape (see
+// tw_offset), read through the read-only data cache.
 template <class T>
 struct TwGlobal {
     const T* __restrict__ p;
-    __device__ __forceinline__ T operator()(int k) const { return __ldg(p + k); }
+    __device__ __forceinline__ T operator()(int idx) const { return __ldg(p + idx); }
 };
 
 // Pass k on NA independent arrays held back to back in v (array a in
@@ -258,7 +265,7 @@ __device__ __forceinline__ void fft_pass(T* v, const TW& tw, int tau) {
     constexpr int R = Sh::radix(k);
     constexpr int N = Sh::sub(k);
     constexpr int Q = N / R;
-    constexpr int STR = S / N;
+    constexpr int OFF = Sh::tw_offset(k);
 #pragma unroll
     for (int beta = 0; beta < E / R; ++beta) {
         const int nu = tau + Sh::T * beta;
@@ -270,7 +277,7 @@ __device__ __forceinline__ void fft_pass(T* v, const TW& tw, int tau) {
         if constexpr (Q > 1) {
 #pragma unroll
             for (int k1 = 1; k1 < R; ++k1) {
-                const T w = tw(c * k1 * STR);
+                const T w = tw(OFF + (k1 - 1) * Q + c);   // zeta_{N_k}^{c k1}
 #pragma unroll
                 for (int a = 0; a < NA; ++a) {
                     T& x = v[a * E + beta * R + k1];

@@ -152,8 +152,8 @@ hd_status plan_finish(const hd_desc* d, const AxisPlan& ax, hd_plan** out) {
         return HD_ERR_CUDA;
     }
     pl->instance_elems = ax.Ls;
-    hd_status st = upload_table(ax.S, d->dtype, &pl->ax[0].twS);
-    if (st == HD_OK) st = upload_table(ax.S * ax.n, d->dtype, &pl->ax[0].twN);
+    hd_status st = upload_fft_twiddles(ax.S, ax.E, d->dtype, &pl->ax[0].twS);
+    if (st == HD_OK) st = upload_twists(ax.S, ax.n, d->dtype, &pl->ax[0].twN);
     if (st != HD_OK) {
         plan_free(pl);
         return st;

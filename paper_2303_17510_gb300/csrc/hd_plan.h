@@ -5,6 +5,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <utility>
 #include <vector>
 
 #include "../../include/hd.h"
@@ -28,14 +29,16 @@ struct AxisPlan {
     bool comp;         // compensated residue accumulation (FP32)
     int minb;          // kernel variant: CTAs per SM of the register allocation
     int path;
-    void* twS;         // zeta_S^k, k < S (device)
-    void* twN;         // zeta_N^k, k < N = n S (device)
+    void* twS;         // FFT pass twiddles of (S, E) (device)
+    void* twN;         // residue twists, see upload_twists (device)
 };
 
 int64_t ceil_div(int64_t a, int64_t b);
 bool is_pow2(int64_t x);
 void zeta_fp64(int64_t k, int64_t N, double* c, double* s);
-hd_status upload_table(int64_t N, int dtype, void** dev);
+hd_status upload_zetas(const std::vector<std::pair<int64_t, int64_t>>& ek, int dtype, void** dev);
+hd_status upload_fft_twiddles(int64_t S, int E, int dtype, void** dev);
+hd_status upload_twists(int64_t S, int64_t n, int dtype, void** dev);
 int max_fused_S(int dtype);
 void axis_geometry(int kind, int64_t L, int64_t m, int64_t p, int64_t q, int64_t* S, int64_t* n, int* nb);
 hd_status validate_axis(int kind, int mult, int64_t L, int64_t M, int64_t m, int64_t p, int64_t q, int64_t* S,
