@@ -25,7 +25,9 @@
 // an R_k-point DFT over the R_k values of sub-problem b at c + i Q_k, then
 // the twiddle zeta_{N_k}^{c k1}.  Result k1 of nu goes to shared slot
 // nu + (S/R_k) k1 (conflict-free, consecutive tau), from which pass k+1
-// reads.  Shared slots use the conflict-free layouts of xslot.
+// reads.  Shared addresses are padded by one element every 16 (a + a/16),
+// which keeps these exchange patterns free of bank conflicts for 8-byte
+// elements (and within 2-way for E = 8 at the Q = 8 read).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -239,17 +241,6 @@ struct FftShape {
 
 __device__ __forceinline__ int padidx(int a) { return a + (a >> 4); }
 
-// Shared slot of exchange element a.  An exchange whose next pass has the full
-// radix E uses an XOR swizzle of the low four bits with the bits above log2 E
-// (a permutation within 16-element rows); the others pad one element per 16.
-// Both are free of bank conflicts for the exchange patterns of E = 4, 8, 16
-// (8-byte elements, half-warp phases).
-template <int LE, bool SWZ>
-__device__ __forceinline__ int xslot(int a) {
-    if constexpr (SWZ) return (a & ~15) | ((a ^ (a >> LE)) & 15);
-    else return a + (a >> 4);
-}
-
 template <class T>
 __device__ __forceinline__ T ldtw(const T* p) {
     return __ldg(p);
@@ -312,7 +303,6 @@ __device__ __forceinline__ void fft_exchange(T* v, T* sm, int tau) {
     constexpr int V = S / R;
     constexpr int Rn = Sh::radix(k + 1);
     constexpr int Qn = Sh::sub(k + 1) / Rn;
-    constexpr bool SWZ = (Rn == E);
     if constexpr (FWD) {
 #pragma unroll
         for (int beta = 0; beta < E / R; ++beta) {
@@ -320,8 +310,7 @@ __device__ __forceinline__ void fft_exchange(T* v, T* sm, int tau) {
 #pragma unroll
             for (int k1 = 0; k1 < R; ++k1)
 #pragma unroll
-                for (int a = 0; a < NA; ++a)
-                    sm[a * Sh::SMEM + xslot<Sh::LE, SWZ>(nu + V * k1)] = v[a * E + beta * R + k1];
+                for (int a = 0; a < NA; ++a) sm[a * Sh::SMEM + padidx(nu + V * k1)] = v[a * E + beta * R + k1];
         }
         __syncthreads();
 #pragma unroll
@@ -332,7 +321,7 @@ __device__ __forceinline__ void fft_exchange(T* v, T* sm, int tau) {
             for (int i = 0; i < Rn; ++i)
 #pragma unroll
                 for (int a = 0; a < NA; ++a)
-                    v[a * E + beta * Rn + i] = sm[a * Sh::SMEM + xslot<Sh::LE, SWZ>(b * Rn * Qn + i * Qn + c)];
+                    v[a * E + beta * Rn + i] = sm[a * Sh::SMEM + padidx(b * Rn * Qn + i * Qn + c)];
         }
         __syncthreads();
     } else {
@@ -344,7 +333,7 @@ __device__ __forceinline__ void fft_exchange(T* v, T* sm, int tau) {
             for (int i = 0; i < Rn; ++i)
 #pragma unroll
                 for (int a = 0; a < NA; ++a)
-                    sm[a * Sh::SMEM + xslot<Sh::LE, SWZ>(b * Rn * Qn + i * Qn + c)] = v[a * E + beta * Rn + i];
+                    sm[a * Sh::SMEM + padidx(b * Rn * Qn + i * Qn + c)] = v[a * E + beta * Rn + i];
         }
         __syncthreads();
 #pragma unroll
@@ -353,8 +342,7 @@ __device__ __forceinline__ void fft_exchange(T* v, T* sm, int tau) {
 #pragma unroll
             for (int k1 = 0; k1 < R; ++k1)
 #pragma unroll
-                for (int a = 0; a < NA; ++a)
-                    v[a * E + beta * R + k1] = sm[a * Sh::SMEM + xslot<Sh::LE, SWZ>(nu + V * k1)];
+                for (int a = 0; a < NA; ++a) v[a * E + beta * R + k1] = sm[a * Sh::SMEM + padidx(nu + V * k1)];
         }
         __syncthreads();
     }
