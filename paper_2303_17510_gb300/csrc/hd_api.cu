@@ -130,6 +130,27 @@ hd_status upload_twists(int64_t S, int64_t n, int dtype, void** dev) {
 
 int max_fused_S(int dtype) { return dtype == HD_F64 ? 2048 : 4096; }
 
+int64_t split_rows(int dtype) { return max_fused_S(dtype); }
+
+bool split_supported(int dtype, int kind, int mult, int64_t S, int nb) {
+    (void)kind;
+    (void)mult;
+    (void)nb;
+    const int64_t S2 = split_rows(dtype);
+    if (!is_pow2(S) || S <= max_fused_S(dtype)) return false;
+    const int64_t S1 = S / S2;
+    return S1 >= 2 && S1 <= 16;
+}
+
+// zeta_S^{j2 k1} at k1 S2 + j2 (k1 < S1, j2 < S2), S = S1 S2.
+hd_status upload_split_twiddles(int64_t S1, int64_t S2, int dtype, void** dev) {
+    std::vector<std::pair<int64_t, int64_t>> ek;
+    ek.reserve((size_t)(S1 * S2));
+    for (int64_t k1 = 0; k1 < S1; ++k1)
+        for (int64_t j2 = 0; j2 < S2; ++j2) ek.emplace_back(j2 * k1, S1 * S2);
+    return upload_zetas(ek, dtype, dev);
+}
+
 // Transform size, residue count and folded blocks of a validated axis plan.
 void axis_geometry(int kind, int64_t L, int64_t m, int64_t p, int64_t q, int64_t* S, int64_t* n, int* nb) {
     if (p == 1 && q == 1) {                    // explicit padding: one residue of size m >= M

@@ -31,6 +31,11 @@ int conv1d_variants(int dtype, int kind, Conv1dCfg* out, int cap);
 // forward transform of residue r of one input (debug path)
 cudaError_t forward_residue_launch(const Conv1dCfg& c, const ConvArgs& a, int r, int m, void* out, cudaStream_t st);
 
+struct SplitArgs;
+// split path: colfwd / row / colbwd kernels for one chunk of instances
+cudaError_t split_launch_f32(const SplitArgs& a, int kind, int mult, bool comp, cudaStream_t st);
+cudaError_t split_launch_f64(const SplitArgs& a, int kind, int mult, bool comp, cudaStream_t st);
+
 // per translation unit entry points (dtype x kind)
 #define HD_DECL_TU(DT, KN)                                                                                   \
     bool conv1d_available_##DT##_##KN(const Conv1dCfg& c, int ls_pad);                                                    \

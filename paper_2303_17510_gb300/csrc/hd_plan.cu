@@ -7,6 +7,7 @@
 #include <new>
 
 #include "hd_plan.h"
+#include "hd_split.cuh"
 
 namespace hd {
 
@@ -84,6 +85,14 @@ hd_status fill_axis(int dtype, int kind, int mult, int64_t L, int64_t M, int64_t
         ax->path = PATH_FUSED;
         return HD_OK;
     }
+    if (split_supported(dtype, kind, mult, S, nb)) {
+        ax->path = PATH_SPLIT;
+        ax->S2 = split_rows(dtype);
+        ax->S1 = S / ax->S2;
+        ax->E = 8;
+        ax->minb = 1;
+        return HD_OK;
+    }
     return HD_ERR_UNSUPPORTED;
 }
 
@@ -96,6 +105,7 @@ hd_status choose_axis(int dtype, int kind, int mult, int A, int B, int64_t L, in
         AxisPlan ax;
         if (fill_axis(dtype, kind, mult, L, M, m, p, q, 1, &ax) != HD_OK) return;
         double c = cost_model(kind, A, B, ax.S, ax.n);
+        if (ax.path == PATH_SPLIT) c *= 1.6;   // work buffer round trips through L2
         // ties (within 1%): smaller qm, then smaller m
         bool better = !found || c < best_cost * 0.99 ||
                       (c <= best_cost * 1.01 &&
@@ -152,8 +162,32 @@ hd_status plan_finish(const hd_desc* d, const AxisPlan& ax, hd_plan** out) {
         return HD_ERR_CUDA;
     }
     pl->instance_elems = ax.Ls;
-    hd_status st = upload_fft_twiddles(ax.S, ax.E, d->dtype, &pl->ax[0].twS);
-    if (st == HD_OK) st = upload_twists(ax.S, ax.n, d->dtype, &pl->ax[0].twN);
+    AxisPlan& a0 = pl->ax[0];
+    a0.twS2 = nullptr;
+    hd_status st;
+    if (a0.path == PATH_FUSED) {
+        st = upload_fft_twiddles(a0.S, a0.E, d->dtype, &a0.twS);
+    } else {
+        st = upload_split_twiddles(a0.S1, a0.S2, d->dtype, &a0.twS);
+        if (st == HD_OK) st = upload_fft_twiddles(a0.S2, a0.E, d->dtype, &a0.twS2);
+        if (st == HD_OK) {
+            // work buffer of Section 5: A n S values per instance, a chunk of
+            // instances at a time (up to 64 instances or 128 MiB)
+            const size_t esz = d->dtype == HD_F64 ? 16 : 8;
+            const size_t per = (size_t)d->A * (size_t)a0.n * (size_t)a0.S * esz;
+            int64_t ch = (int64_t)((128u << 20) / per);
+            if (ch > 64) ch = 64;
+            if (ch < 1) ch = 1;
+            a0.chunk = ch;
+            pl->scratch_bytes = per * (size_t)ch;
+            if (cudaMalloc(&pl->scratch, pl->scratch_bytes) != cudaSuccess) {
+                cudaGetLastError();
+                pl->scratch = nullptr;
+                st = HD_ERR_NOMEM;
+            }
+        }
+    }
+    if (st == HD_OK) st = upload_twists(a0.S, a0.n, d->dtype, &a0.twN);
     if (st != HD_OK) {
         plan_free(pl);
         return st;
@@ -171,12 +205,13 @@ hd_status plan_create_from(hd_plan** out, const hd_desc* d, const hd_candidate* 
     st = fill_axis(d->dtype, d->kind, d->mult, d->L[0], d->M[0], c->m, c->p, c->q, c->D, &ax);
     if (st != HD_OK && st != HD_ERR_UNSUPPORTED) return st;
     if (ax.S != c->S || ax.n != c->n) return HD_ERR_INVALID;
-    ax.E = c->E;
-    ax.minb = c->minb;
     ax.comp = c->comp != 0 && d->dtype == HD_F32;
-    if (!fused_supported(d->dtype, d->kind, d->mult, ax.S, ax.nb, ax.Ls, ax.comp, ax.E, ax.minb))
-        return HD_ERR_UNSUPPORTED;
-    ax.path = PATH_FUSED;
+    if (ax.path == PATH_FUSED) {
+        ax.E = c->E;
+        ax.minb = c->minb;
+        if (!fused_supported(d->dtype, d->kind, d->mult, ax.S, ax.nb, ax.Ls, ax.comp, ax.E, ax.minb))
+            return HD_ERR_UNSUPPORTED;
+    }
     return plan_finish(d, ax, out);
 }
 
@@ -228,11 +263,53 @@ Conv1dCfg fused_cfg(const hd_plan& pl, const AxisPlan& ax) {
     return c;
 }
 
+SplitArgs make_split_args(const hd_plan& pl, const AxisPlan& ax, int64_t first, int64_t count, const void* const* f,
+                          void* const* h, int64_t stride, void* work) {
+    SplitArgs a;
+    std::memset(&a, 0, sizeof(a));
+    const size_t esz = pl.dtype == HD_F64 ? 16 : 8;
+    for (int i = 0; i < pl.A && i < 3; ++i) a.f[i] = static_cast<const char*>(f[i]) + first * stride * esz;
+    a.h = static_cast<char*>(h[0]) + first * stride * esz;
+    a.stride = stride;
+    a.count = count;
+    a.L = (int)ax.L;
+    a.Ls = (int)ax.Ls;
+    a.H = (int)(ax.L / 2);
+    a.n = (int)ax.n;
+    a.S = (int)ax.S;
+    a.S1 = (int)ax.S1;
+    a.S2 = (int)ax.S2;
+    a.A = pl.A;
+    a.twS = ax.twS;
+    a.twR = ax.twN;
+    a.twS2 = ax.twS2;
+    a.work = work;
+    a.invN = 1.0 / (double)(ax.n * ax.S);
+    return a;
+}
+
+hd_status split_execute(const hd_plan& pl, const AxisPlan& ax, int64_t count, const void* const* f, void* const* h,
+                        int64_t stride, void* work, int64_t chunk, cudaStream_t st) {
+    const int mult = pl.mult == HD_MULT_PRODUCT ? MULT_PRODUCT : MULT_PAIRS3;
+    for (int64_t first = 0; first < count; first += chunk) {
+        const int64_t cnt = count - first < chunk ? count - first : chunk;
+        SplitArgs a = make_split_args(pl, ax, first, cnt, f, h, stride, work);
+        cudaError_t e = pl.dtype == HD_F64 ? split_launch_f64(a, ax.kind, mult, ax.comp, st)
+                                           : split_launch_f32(a, ax.kind, mult, ax.comp, st);
+        if (e != cudaSuccess) return HD_ERR_CUDA;
+    }
+    return HD_OK;
+}
+
 hd_status plan_execute(hd_plan* pl, int64_t count, const void* const* f, void* const* h, int64_t stride,
                        cudaStream_t st) {
     DeviceGuard g(pl->device);
     const AxisPlan& ax = pl->ax[0];
-    if (ax.path != PATH_FUSED) return HD_ERR_UNSUPPORTED;
+    if (ax.path == PATH_SPLIT) {
+        hd_status s2 = split_execute(*pl, ax, count, f, h, stride, pl->scratch, ax.chunk, st);
+        if (s2 != HD_OK) pl->sticky = s2;
+        return s2;
+    }
     ConvArgs a = make_conv_args(*pl, ax, count, f, h, stride);
     cudaError_t e = conv1d_launch(fused_cfg(*pl, ax), a, st);
     if (e != cudaSuccess) {
@@ -249,6 +326,7 @@ void plan_free(hd_plan* pl) {
     for (int i = 0; i < 3; ++i) {
         if (pl->ax[i].twS) cudaFree(pl->ax[i].twS);
         if (pl->ax[i].twN) cudaFree(pl->ax[i].twN);
+        if (pl->ax[i].twS2) cudaFree(pl->ax[i].twS2);
     }
     if (pl->scratch) cudaFree(pl->scratch);
     cudaGetLastError();

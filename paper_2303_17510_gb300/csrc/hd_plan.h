@@ -29,8 +29,11 @@ struct AxisPlan {
     bool comp;         // compensated residue accumulation (FP32)
     int minb;          // kernel variant: CTAs per SM of the register allocation
     int path;
-    void* twS;         // FFT pass twiddles of (S, E) (device)
+    void* twS;         // FUSED: FFT pass twiddles of (S, E); SPLIT: zeta_S^{j2 k1} (device)
     void* twN;         // residue twists, see upload_twists (device)
+    void* twS2;        // SPLIT: FFT pass twiddles of the row FFT (device)
+    int64_t S1, S2;    // SPLIT: S = S1 * S2
+    int64_t chunk;     // SPLIT: instances per scratch chunk
 };
 
 int64_t ceil_div(int64_t a, int64_t b);
@@ -45,6 +48,10 @@ hd_status validate_axis(int kind, int mult, int64_t L, int64_t M, int64_t m, int
                         int64_t* n, int* nb);
 bool fused_supported(int dtype, int kind, int mult, int64_t S, int nb, int64_t Ls, bool comp, int E, int minb);
 int default_minb(int dtype, int64_t S);
+// split path (transforms larger than one CTA): S = S1 * S2, S2 the fused limit, S1 <= 16
+bool split_supported(int dtype, int kind, int mult, int64_t S, int nb);
+int64_t split_rows(int dtype);
+hd_status upload_split_twiddles(int64_t S1, int64_t S2, int dtype, void** dev);
 // staged row length in shared memory for Ls stored values (even: 16-byte rows)
 inline int64_t staged_row(int64_t Ls) { return (Ls + 1) & ~int64_t(1); }
 double cost_model(int kind, int A, int B, int64_t S, int64_t n);
@@ -60,7 +67,7 @@ struct hd_plan {
     hd::AxisPlan ax[3];
     int64_t instance_elems;   // stored elements of one instance (all axes)
     size_t scratch_bytes;
-    void* scratch;
+    void* scratch;     // split-path work buffer (chunk * A * n * S values)
     int device;
     hd_status sticky;
 };

@@ -1,0 +1,214 @@
+// hd_split.cuh -- residue transforms larger than one CTA (the "split" path).
+//
+// A residue transform of size S = S1 * S2 (S2 <= the fused limit, S1 <= 16)
+// is computed in the order of the paper's inner loop (Section 5.1,
+// forwardInner / backwardInner): size-S1 DFTs along the block index t (here
+// j1), the twiddle zeta_S^{j2 k1}, then size-S2 FFTs along s (here j2):
+//     X_{k1 + S1 k2} = sum_{j2} zeta_{S2}^{j2 k2} zeta_S^{j2 k1}
+//                      sum_{j1} zeta_{S1}^{j1 k1} W_{j1 S2 + j2}.
+// Three kernels per batch chunk, with the work buffer of Section 5 (A n S
+// values per instance) in device scratch:
+//   split_colfwd : per (instance, input a, residue r, column j2): fold and twist
+//                  the stored input into W_{j1 S2 + j2}, DFT over j1, twiddle,
+//                  store row k1 of the work buffer;
+//   split_row    : per (instance, residue, row k1): FFT_{S2} of the A rows, mult,
+//                  inverse FFT_{S2}, result written over row k1 of input 0;
+//   split_colbwd : per (instance, column j2): for every residue the conjugate
+//                  twiddle and inverse DFT over k1, then the residue contribution
+//                  zeta_N^{-r i} y_{i mod S} accumulated into the output (all
+//                  residues in registers, one store).
+// Hermitian residues are not paired here: the residue's spectrum is real and
+// the inverse of a real spectrum is Hermitian, so y is used directly.
+#pragma once
+
+#include "hd_conv1d.cuh"
+
+namespace hd {
+
+struct SplitArgs {
+    const void* f[3];   // A input bases
+    void* h;            // output base
+    int64_t stride;     // elements between instances
+    int64_t count;      // instances in this chunk
+    int L, Ls, H;       // as ConvArgs
+    int n;              // residues
+    int S, S1, S2;      // transform size and its split
+    int A;
+    const void* twS;    // zeta_S^{j2 k1} at k1 S2 + j2 (k1 < S1, j2 < S2)
+    const void* twR;    // residue twists (ConvArgs::twN layout)
+    const void* twS2;   // FFT pass twiddles of the size-S2 row FFT
+    void* work;         // scratch: [instance][a][r][k1][j2]
+    double invN;
+};
+
+template <int S1, bool INV, class T>
+__device__ __forceinline__ void dft_small(T* v) {
+    dft_reg<S1, INV>(v);
+}
+
+// Forward columns: one thread per (instance, a, r, j2), j2 fastest.
+template <class R, int S1, int KIND>
+__global__ void __launch_bounds__(256) split_colfwd(const __grid_constant__ SplitArgs a) {
+    using T = cplx<R>;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t total = a.count * a.A * a.n * (int64_t)a.S2;
+    if (tid >= total) return;
+    const int j2 = (int)(tid % a.S2);
+    int64_t rest = tid / a.S2;
+    const int r = (int)(rest % a.n);
+    rest /= a.n;
+    const int aa = (int)(rest % a.A);
+    const int64_t inst = rest / a.A;
+    const T* f = static_cast<const T*>(a.f[aa]) + inst * a.stride;
+    const T* twR = static_cast<const T*>(a.twR);
+    const T* twS = static_cast<const T*>(a.twS);
+    ConvArgs ca;
+    ca.L = a.L;
+    ca.Ls = a.Ls;
+    ca.H = a.H;
+    T cr = ldtw(twR + (int64_t)a.n * a.S + r);      // zeta_N^{r S}
+    if constexpr (KIND != KIND_COMPLEX) cr = cconj(cr);
+    T v[S1];
+#pragma unroll
+    for (int j1 = 0; j1 < S1; ++j1) {
+        const int j = j1 * a.S2 + j2;
+        T b0, b1;
+        load_fold<KIND>(f, j, a.S, ca, true, b0, b1);
+        v[j1] = cmul(cadd(b0, cmul(cr, b1)), ldtw(twR + (int64_t)r * a.S + j));
+    }
+    dft_small<S1, false>(v);
+    T* w = static_cast<T*>(a.work) + ((inst * a.A + aa) * a.n + r) * (int64_t)a.S;
+#pragma unroll
+    for (int k1 = 0; k1 < S1; ++k1) {
+        const T t = k1 == 0 ? v[0] : cmul(v[k1], ldtw(twS + k1 * a.S2 + j2));
+        w[(int64_t)k1 * a.S2 + j2] = t;
+    }
+}
+
+// Rows: one group of S2/E threads per (instance, residue, row k1).
+template <class R, int S2, int E, int KIND, int MULT>
+__global__ void __launch_bounds__(ConvLaunch<S2, E>::MAXT) split_row(const __grid_constant__ SplitArgs a) {
+    using T = cplx<R>;
+    using Sh = FftShape<S2, E>;
+    constexpr int TT = Sh::T;
+    constexpr int A = (MULT == MULT_PRODUCT) ? 2 : 3;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int G = blockDim.x / TT;
+    const int g = threadIdx.x / TT;
+    const int tau = threadIdx.x - g * TT;
+    T* sm = reinterpret_cast<T*>(smem_raw) + (size_t)g * A * Sh::SMEM;
+    const int64_t row = (int64_t)blockIdx.x * G + g;
+    const int64_t rows = a.count * a.n * (int64_t)a.S1;
+    const bool valid = row < rows;
+    const int k1 = (int)(row % a.S1);
+    const int64_t rr = row / a.S1;
+    const int r = (int)(rr % a.n);
+    const int64_t inst = rr / a.n;
+    const TwGlobal<T> tw{static_cast<const T*>(a.twS2)};
+    T* base = static_cast<T*>(a.work);
+    T v[A * E];
+#pragma unroll
+    for (int aa = 0; aa < A; ++aa) {
+        const T* src = base + ((inst * A + aa) * a.n + r) * (int64_t)a.S + (int64_t)k1 * S2;
+#pragma unroll
+        for (int e = 0; e < E; ++e) v[aa * E + e] = valid ? src[tau + TT * e] : czero<T>();
+    }
+    fft_forward<S2, E, A>(v, sm, tw, tau);
+    T p[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        if constexpr (KIND == KIND_HERMITIAN) {
+            // real residue spectra: mult acts on the real parts
+            const T x0 = v[e], x1 = v[E + e];
+            if constexpr (MULT == MULT_PRODUCT) {
+                p[e] = mk<T>(x0.x * x1.x, 0);
+            } else {
+                const T x2 = v[2 * E + e];
+                p[e] = mk<T>(x0.x * x1.x + x2.x * (x0.x + x1.x), 0);
+            }
+        } else if constexpr (MULT == MULT_PRODUCT) {
+            p[e] = cmul(v[e], v[E + e]);
+        } else {
+            p[e] = cadd(cmul(v[e], v[E + e]), cmul(v[2 * E + e], cadd(v[e], v[E + e])));
+        }
+    }
+    fft_inverse<S2, E, 1>(p, sm, tw, tau);
+    if (!valid) return;
+    T* dst = base + ((inst * A + 0) * a.n + r) * (int64_t)a.S + (int64_t)k1 * S2;
+#pragma unroll
+    for (int e = 0; e < E; ++e) dst[tau + TT * e] = p[e];
+}
+
+// Backward columns: one thread per (instance, j2); all residues accumulated.
+template <class R, int S1, int KIND, bool COMP>
+__global__ void __launch_bounds__(256) split_colbwd(const __grid_constant__ SplitArgs a) {
+    using T = cplx<R>;
+    constexpr int NB = (KIND == KIND_HERMITIAN) ? 1 : 2;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= a.count * (int64_t)a.S2) return;
+    const int j2 = (int)(tid % a.S2);
+    const int64_t inst = tid / a.S2;
+    const T* twR = static_cast<const T*>(a.twR);
+    const T* twS = static_cast<const T*>(a.twS);
+    const T* base = static_cast<const T*>(a.work) + inst * a.A * (int64_t)a.n * a.S;
+    R s0[2 * S1], c0[COMP ? 2 * S1 : 1], s1[NB == 2 ? 2 * S1 : 1], c1[(NB == 2 && COMP) ? 2 * S1 : 1];
+    R dummy = 0;
+#pragma unroll
+    for (int i = 0; i < 2 * S1; ++i) {
+        s0[i] = 0;
+        if constexpr (COMP) c0[i] = 0;
+        if constexpr (NB == 2) {
+            s1[i] = 0;
+            if constexpr (COMP) c1[i] = 0;
+        }
+    }
+    for (int r = 0; r < a.n; ++r) {
+        T cr = ldtw(twR + (int64_t)a.n * a.S + r);
+        if constexpr (KIND != KIND_COMPLEX) cr = cconj(cr);
+        T v[S1];
+#pragma unroll
+        for (int k1 = 0; k1 < S1; ++k1) {
+            const T z = base[(int64_t)r * a.S + (int64_t)k1 * a.S2 + j2];
+            v[k1] = k1 == 0 ? z : cmulc(z, ldtw(twS + k1 * a.S2 + j2));
+        }
+        dft_small<S1, true>(v);
+#pragma unroll
+        for (int j1 = 0; j1 < S1; ++j1) {
+            const int j = j1 * a.S2 + j2;
+            T y = cmulc(v[j1], ldtw(twR + (int64_t)r * a.S + j));
+            acc_add<R, COMP>(s0[2 * j1], COMP ? c0[2 * j1] : dummy, y.x);
+            acc_add<R, COMP>(s0[2 * j1 + 1], COMP ? c0[2 * j1 + 1] : dummy, y.y);
+            if constexpr (NB == 2) {
+                const T y1 = cmulc(y, cr);
+                acc_add<R, COMP>(s1[2 * j1], COMP ? c1[2 * j1] : dummy, y1.x);
+                acc_add<R, COMP>(s1[2 * j1 + 1], COMP ? c1[2 * j1 + 1] : dummy, y1.y);
+            }
+        }
+    }
+    T* hout = static_cast<T*>(a.h) + inst * a.stride;
+    const R sc = R(a.invN);
+#pragma unroll
+    for (int j1 = 0; j1 < S1; ++j1) {
+        const int j = j1 * a.S2 + j2;
+        const R x0 = COMP ? s0[2 * j1] + c0[2 * j1] : s0[2 * j1];
+        const R y0 = COMP ? s0[2 * j1 + 1] + c0[2 * j1 + 1] : s0[2 * j1 + 1];
+        const T o0 = mk<T>(x0 * sc, y0 * sc);
+        T o1 = czero<T>();
+        if constexpr (NB == 2) {
+            const R x1 = COMP ? s1[2 * j1] + c1[2 * j1] : s1[2 * j1];
+            const R y1 = COMP ? s1[2 * j1 + 1] + c1[2 * j1 + 1] : s1[2 * j1 + 1];
+            o1 = mk<T>(x1 * sc, y1 * sc);
+        }
+        if constexpr (KIND == KIND_COMPLEX) {
+            if (j < a.L) hout[j] = o0;
+            if (j + a.S < a.L) hout[j + a.S] = o1;
+        } else if constexpr (KIND == KIND_CENTERED) {
+            if (j < a.L - a.H) hout[j + a.H] = o0;
+            if (j >= a.S - a.H) hout[j - a.S + a.H] = o1;
+        } else {
+            if (j < a.Ls) hout[j] = o0;
+        }
+    }
+}
+
+}  // namespace hd

@@ -68,6 +68,33 @@ int enumerate_candidates(const hd_desc* d, std::vector<hd_candidate>* out) {
         int nb;
         if (validate_axis(d->kind, d->mult, L, M, m, p, q, &S, &n, &nb) != HD_OK) continue;
         const int64_t Ls = d->kind == HD_HERMITIAN ? (L + 1) / 2 : L;
+        if (split_supported(d->dtype, d->kind, d->mult, S, nb)) {
+            bool dup = false;
+            for (auto& c : *out)
+                if (c.S == S && c.n == n) {
+                    if (p < c.p) {
+                        c.m = m;
+                        c.p = p;
+                        c.q = q;
+                    }
+                    dup = true;
+                }
+            if (!dup) {
+                hd_candidate c;
+                std::memset(&c, 0, sizeof(c));
+                c.m = m;
+                c.p = p;
+                c.q = q;
+                c.D = 1;
+                c.S = S;
+                c.n = n;
+                c.E = 8;
+                c.minb = 1;
+                c.comp = comp ? 1 : 0;
+                out->push_back(c);
+            }
+            continue;
+        }
         for (int v = 0; v < nv && v < 64; ++v) {
             if (vars[v].S != S) continue;
             if (!fused_supported(d->dtype, d->kind, d->mult, S, nb, Ls, comp, vars[v].E, vars[v].minb)) continue;
