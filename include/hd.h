@@ -55,7 +55,8 @@ typedef enum {
     HD_ERR_NOMEM = 3,
     HD_ERR_CUDA = 4,
     HD_ERR_TIMEOUT = 5,
-    HD_ERR_ALIASED = 6
+    HD_ERR_ALIASED = 6,
+    HD_ERR_SCRATCH_LIMIT = 7
 } hd_status;
 
 enum { HD_COMPLEX = 0, HD_CENTERED = 1, HD_HERMITIAN = 2 };
@@ -187,6 +188,38 @@ hd_status hd_plan_create_candidate(hd_plan** out, const hd_desc* d, const hd_can
 hd_status hd_tune_cache_put(const hd_desc* d, const hd_candidate* c);
 hd_status hd_tune_cache_get(const hd_desc* d, hd_candidate* c);
 hd_status hd_tune_cache_clear(void);
+
+/* ---------------------------------------------------------------------------
+ * Allocation-free batched convolution (no counterpart in the paper).
+ *
+ * Some callers cannot allocate device memory when they convolve: a service
+ * that reserves all of its GPU memory at start-up and must not grow it while
+ * serving, code that runs inside another runtime's memory manager, or a hot
+ * loop where a device allocation would synchronize the device and stall other
+ * streams.  For plans whose residue transforms are too large for one CTA (the
+ * split path, which needs a work buffer of A * n * S values per instance),
+ * this entry point uses a fixed work buffer that is part of the library image
+ * on each GPU instead of the plan's own buffer, and itself calls no device
+ * allocation or free.  The plan is still created beforehand (plan creation
+ * allocates its twiddle tables).
+ *
+ *   - The fixed buffer holds HD_NOALLOC_SCRATCH_BYTES bytes on every GPU that
+ *     loads the library, until the process exits.  Batches are processed in
+ *     chunks that fit it; a plan whose single instance needs more returns
+ *     HD_ERR_SCRATCH_LIMIT before launching anything.
+ *   - The first call on a device looks up the buffer's device address on that
+ *     device (the device current at the call); make that first call before any
+ *     stream capture begins.
+ *   - All calls share the buffer and it keeps the last call's contents.  The
+ *     kernels write every work-buffer entry before they read it, so nothing
+ *     needs clearing, but calls whose kernels overlap on the GPU (different
+ *     streams, or several host threads) race on the buffer: order them on one
+ *     stream or synchronize between them.
+ *   - Plans that use no work buffer (the fused path) return HD_ERR_UNSUPPORTED.
+ * Arguments and results are those of hd_convolve_batched. */
+#define HD_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+hd_status hd_convolve_batched_noalloc(const hd_plan* plan, int64_t count, const void* const* f, void* const* h,
+                                      int64_t batch_stride, void* stream);
 
 /* Releases the plan's device memory (after synchronizing its device). NULL ok. */
 hd_status hd_plan_destroy(hd_plan* plan);

@@ -26,7 +26,7 @@ KIND = {"complex": 0, "centered": 1, "hermitian": 2}
 DTYPE = {"f32": 0, "f64": 1}
 MULT = {"product": 0, "sum_pairs3": 1}
 STATUS = {0: "HD_OK", 1: "HD_ERR_INVALID", 2: "HD_ERR_UNSUPPORTED", 3: "HD_ERR_NOMEM", 4: "HD_ERR_CUDA",
-          5: "HD_ERR_TIMEOUT", 6: "HD_ERR_ALIASED"}
+          5: "HD_ERR_TIMEOUT", 6: "HD_ERR_ALIASED", 7: "HD_ERR_SCRATCH_LIMIT"}
 _i64 = ctypes.c_int64
 _vp = ctypes.c_void_p
 
@@ -81,6 +81,7 @@ _sig("hd_plan_create_candidate", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POIN
 _sig("hd_tune_cache_put", ctypes.c_int, [ctypes.POINTER(hd_desc), ctypes.POINTER(hd_candidate)])
 _sig("hd_tune_cache_get", ctypes.c_int, [ctypes.POINTER(hd_desc), ctypes.POINTER(hd_candidate)])
 _sig("hd_tune_cache_clear", ctypes.c_int, [])
+_sig("hd_convolve_batched_noalloc", ctypes.c_int, [_vp, _i64, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i64, _vp])
 
 
 def _check(rc, where):
@@ -217,6 +218,13 @@ class Plan:
         ha = (_vp * self.B)(*[_ptr(h)] if not isinstance(h, (list, tuple)) else [_ptr(x) for x in h])
         _check(lib.hd_convolve_batched(self._h, int(count), fa, ha, int(batch_stride), _stream(stream)),
                "hd_convolve_batched")
+
+    def convolve_batched_noalloc(self, fs, h, count, batch_stride, stream=None):
+        """As convolve_batched, over the library's fixed work buffer (no device allocation)."""
+        fa = (_vp * self.A)(*[_ptr(x) for x in fs])
+        ha = (_vp * self.B)(*[_ptr(h)] if not isinstance(h, (list, tuple)) else [_ptr(x) for x in h])
+        _check(lib.hd_convolve_batched_noalloc(self._h, int(count), fa, ha, int(batch_stride), _stream(stream)),
+               "hd_convolve_batched_noalloc")
 
     def forward_residue(self, f, r, out, stream=None):
         _check(lib.hd_forward_residue(self._h, _ptr(f), int(r), _ptr(out), _stream(stream)), "hd_forward_residue")

@@ -259,6 +259,8 @@ const char* hd_status_string(hd_status s) {
         case HD_ERR_CUDA: return "HD_ERR_CUDA: CUDA error";
         case HD_ERR_TIMEOUT: return "HD_ERR_TIMEOUT: bounded device wait expired";
         case HD_ERR_ALIASED: return "HD_ERR_ALIASED: M is below the dealiasing bound";
+        case HD_ERR_SCRATCH_LIMIT:
+            return "HD_ERR_SCRATCH_LIMIT: one instance needs more work buffer than the fixed allocation-free buffer";
     }
     return "unknown hd_status";
 }

@@ -90,6 +90,10 @@ int enumerate_candidates(const hd_desc* d, std::vector<hd_candidate>* out);
 // tuned candidate recorded for the description, if any
 bool cache_lookup(const hd_desc* d, hd_candidate* c);
 
+// Split path over a caller-provided work buffer holding `chunk` instances.
+hd_status split_execute(const hd_plan& pl, const AxisPlan& ax, int64_t count, const void* const* f, void* const* h,
+                        int64_t stride, void* work, int64_t chunk, cudaStream_t st);
+
 // Legal, supported (m, p, q) of one axis chosen by the cost model; fills ax.
 hd_status choose_axis(int dtype, int kind, int mult, int A, int B, int64_t L, int64_t M, AxisPlan* ax);
 

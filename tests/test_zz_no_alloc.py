@@ -1,0 +1,84 @@
+"""GPU test of hd_convolve_batched_noalloc, the allocation-free batched call.
+
+It serves callers that cannot allocate device memory while they convolve (a
+service that reserves its GPU memory at start-up, code inside another
+runtime's memory manager, a hot loop that must not synchronize the device on
+an allocation).  It runs the split path over the library's fixed work buffer
+instead of the plan's own.  The test calls it through the C ABI twice in a
+row and compares each result with hd_convolve_batched on the same plan and
+inputs, within the FP32 tolerance of the other parity tests (rel-L2 <= 1e-5);
+it also checks the size limit and that plans without a work buffer are
+refused.  It is self-contained, so it runs alone in a fresh process as well
+as after the other tests.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import inputs
+
+pytestmark = pytest.mark.gpu
+
+F32_TOL = 1e-5
+NOALLOC_BYTES = 32 << 20       # HD_NOALLOC_SCRATCH_BYTES in include/hd.h
+
+
+def _rel_l2(got, ref):
+    return float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+
+
+@pytest.fixture(scope="module")
+def hd():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2303_17510_gb300 as hd
+    return hd
+
+
+def _call(b, plan, count, fs, h, stride):
+    import torch
+    fa = (ctypes.c_void_p * len(fs))(*[x.data_ptr() for x in fs])
+    ha = (ctypes.c_void_p * 1)(h.data_ptr())
+    return b.lib.hd_convolve_batched_noalloc(ctypes.c_void_p(plan.handle), count, fa, ha, stride,
+                                              ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+
+
+def test_noalloc_matches_batched_on_two_calls(hd):
+    import torch
+    from paper_2303_17510_gb300 import _binding as b
+
+    L, M, count = 9000, 18010, 70
+    cand = [c for c in hd.enumerate_candidates(L=L, M=M) if c["S"] > 4096][0]
+    per_instance = 2 * cand["n"] * cand["S"] * 8
+    assert count * per_instance > NOALLOC_BYTES          # the batch needs more than one chunk
+    f = [torch.from_numpy(inputs.uniform_complex((count, L), 900 + a, dtype=np.complex64)).cuda() for a in range(2)]
+    with hd.Plan(L, M, candidate=cand) as plan:
+        ref = torch.empty_like(f[0])
+        plan.convolve_batched(f, ref, count, L)
+        torch.cuda.synchronize()
+        want = ref.cpu().numpy().astype(np.complex128)
+        for call in range(2):
+            out = torch.full_like(f[0], float("nan"))
+            rc = _call(b, plan, count, f, out, L)
+            assert rc == 0, b.STATUS.get(rc, rc)
+            torch.cuda.synchronize()
+            got = out.cpu().numpy().astype(np.complex128)
+            assert np.all(np.isfinite(got)), call
+            assert _rel_l2(got, want) <= F32_TOL, call
+
+
+def test_noalloc_rejects_oversize_and_fused_plans(hd):
+    import torch
+    from paper_2303_17510_gb300 import _binding as b
+
+    # one instance needs A n S * 8 bytes = 2 * 33 * 65536 * 8 > 32 MiB
+    L, M = 60000, 33 * 65536
+    cand = [c for c in hd.enumerate_candidates(L=L, M=M) if c["S"] == 65536][0]
+    assert 2 * cand["n"] * cand["S"] * 8 > NOALLOC_BYTES
+    x = torch.zeros(L, dtype=torch.complex64, device="cuda")
+    with hd.Plan(L, M, candidate=cand) as plan:
+        assert b.STATUS[_call(b, plan, 1, [x, x], x, L)] == "HD_ERR_SCRATCH_LIMIT"
+    with hd.Plan(1024, 2047) as plan:                        # fused path: no work buffer
+        y = torch.zeros(1024, dtype=torch.complex64, device="cuda")
+        assert b.STATUS[_call(b, plan, 1, [y, y], y, 1024)] == "HD_ERR_UNSUPPORTED"
