@@ -137,6 +137,11 @@ hd_status hd_convolve_batched(const hd_plan* plan, int64_t count, const void* co
 hd_status hd_plan_get_params(const hd_plan* plan, int64_t* m, int64_t* p, int64_t* q, int* D,
                              size_t* scratch_bytes);
 
+/* Parameters of one axis (0 = outermost) of a plan: (m, p, q, D) as in the
+ * paper, the residue transform size S and the residue count n. */
+hd_status hd_plan_get_axis_params(const hd_plan* plan, int axis, int64_t* m, int64_t* p, int64_t* q, int* D,
+                                  int64_t* S, int64_t* n);
+
 /* Residue contribution r of one stored 1D input (the forward residue
  * transform alone, without mult or the backward transform).  Writes the values of residue r in the order the
  * paper's transforms return them (Section 2.2 forward1/forward2: F_{q l + r},

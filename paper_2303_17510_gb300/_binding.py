@@ -71,6 +71,9 @@ _sig("hd_convolve_batched", ctypes.c_int, [_vp, _i64, ctypes.POINTER(_vp), ctype
 _sig("hd_plan_get_params", ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64),
                                           ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_size_t)])
 _sig("hd_forward_residue", ctypes.c_int, [_vp, _vp, _i64, _vp, _vp])
+_sig("hd_plan_get_axis_params", ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(_i64), ctypes.POINTER(_i64),
+                                               ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_i64),
+                                               ctypes.POINTER(_i64)])
 _sig("hd_plan_destroy", ctypes.c_int, [_vp])
 _sig("hd_enumerate_candidates", ctypes.c_int, [ctypes.POINTER(hd_desc), ctypes.POINTER(hd_candidate), ctypes.c_int,
                                                ctypes.POINTER(ctypes.c_int)])
@@ -206,6 +209,13 @@ class Plan:
         _check(lib.hd_plan_get_params(self._h, ctypes.byref(m), ctypes.byref(p), ctypes.byref(q), ctypes.byref(D),
                                       ctypes.byref(s)), "hd_plan_get_params")
         return dict(m=m.value, p=p.value, q=q.value, D=D.value, scratch_bytes=s.value)
+
+    def axis_params(self, axis):
+        m, p, q, S, n = _i64(), _i64(), _i64(), _i64(), _i64()
+        D = ctypes.c_int()
+        _check(lib.hd_plan_get_axis_params(self._h, int(axis), ctypes.byref(m), ctypes.byref(p), ctypes.byref(q),
+                                           ctypes.byref(D), ctypes.byref(S), ctypes.byref(n)), "hd_plan_get_axis_params")
+        return dict(m=m.value, p=p.value, q=q.value, D=D.value, S=S.value, n=n.value)
 
     def convolve(self, fs, h, stream=None):
         """One convolution: fs = A device arrays (tensors or addresses), h = output."""

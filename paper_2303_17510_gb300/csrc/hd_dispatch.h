@@ -36,6 +36,14 @@ struct SplitArgs;
 cudaError_t split_launch_f32(const SplitArgs& a, int kind, int mult, bool comp, cudaStream_t st);
 cudaError_t split_launch_f64(const SplitArgs& a, int kind, int mult, bool comp, cudaStream_t st);
 
+struct ColArgs;
+// outer-axis column kernels (forward or backward) for one residue block
+cudaError_t col_launch_f32(const ColArgs& a, int kind, bool comp, bool fwd, cudaStream_t st);
+cudaError_t col_launch_f64(const ColArgs& a, int kind, bool comp, bool fwd, cudaStream_t st);
+// values per thread of the column FFT of size S (its twiddle table layout)
+int col_E_of_f32(int S);
+int col_E_of_f64(int S);
+
 // per translation unit entry points (dtype x kind)
 #define HD_DECL_TU(DT, KN)                                                                                   \
     bool conv1d_available_##DT##_##KN(const Conv1dCfg& c, int ls_pad);                                                    \

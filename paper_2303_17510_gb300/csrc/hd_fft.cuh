@@ -295,8 +295,10 @@ __device__ __forceinline__ void fft_pass(T* v, const TW& tw, int tau) {
 // Exchange between pass k and pass k+1 for NA arrays (array a uses the padded
 // buffer sm + a * SMEM).  FWD: from the layout after pass k to the layout pass
 // k+1 reads; otherwise the reverse.  Two barriers: after the writes, and
-// before the buffers are written again.
-template <int S, int E, int k, bool FWD, int NA, class T>
+// before the buffers are written again.  CST > 1 interleaves the buffers of
+// CST independent transforms (one per column of a column tile): slot s of the
+// transform held by this thread is at sm[s * CST], sm pointing at its column.
+template <int S, int E, int k, bool FWD, int NA, int CST, class T>
 __device__ __forceinline__ void fft_exchange(T* v, T* sm, int tau) {
     using Sh = FftShape<S, E>;
     constexpr int R = Sh::radix(k);
@@ -310,7 +312,7 @@ __device__ __forceinline__ void fft_exchange(T* v, T* sm, int tau) {
 #pragma unroll
             for (int k1 = 0; k1 < R; ++k1)
 #pragma unroll
-                for (int a = 0; a < NA; ++a) sm[a * Sh::SMEM + padidx(nu + V * k1)] = v[a * E + beta * R + k1];
+                for (int a = 0; a < NA; ++a) sm[(a * Sh::SMEM + padidx(nu + V * k1)) * CST] = v[a * E + beta * R + k1];
         }
         __syncthreads();
 #pragma unroll
@@ -321,7 +323,7 @@ __device__ __forceinline__ void fft_exchange(T* v, T* sm, int tau) {
             for (int i = 0; i < Rn; ++i)
 #pragma unroll
                 for (int a = 0; a < NA; ++a)
-                    v[a * E + beta * Rn + i] = sm[a * Sh::SMEM + padidx(b * Rn * Qn + i * Qn + c)];
+                    v[a * E + beta * Rn + i] = sm[(a * Sh::SMEM + padidx(b * Rn * Qn + i * Qn + c)) * CST];
         }
         __syncthreads();
     } else {
@@ -333,7 +335,7 @@ __device__ __forceinline__ void fft_exchange(T* v, T* sm, int tau) {
             for (int i = 0; i < Rn; ++i)
 #pragma unroll
                 for (int a = 0; a < NA; ++a)
-                    sm[a * Sh::SMEM + padidx(b * Rn * Qn + i * Qn + c)] = v[a * E + beta * Rn + i];
+                    sm[(a * Sh::SMEM + padidx(b * Rn * Qn + i * Qn + c)) * CST] = v[a * E + beta * Rn + i];
         }
         __syncthreads();
 #pragma unroll
@@ -342,41 +344,41 @@ __device__ __forceinline__ void fft_exchange(T* v, T* sm, int tau) {
 #pragma unroll
             for (int k1 = 0; k1 < R; ++k1)
 #pragma unroll
-                for (int a = 0; a < NA; ++a) v[a * E + beta * R + k1] = sm[a * Sh::SMEM + padidx(nu + V * k1)];
+                for (int a = 0; a < NA; ++a) v[a * E + beta * R + k1] = sm[(a * Sh::SMEM + padidx(nu + V * k1)) * CST];
         }
         __syncthreads();
     }
 }
 
-template <int S, int E, int k, int NA, class T, class TW>
+template <int S, int E, int k, int NA, int CST, class T, class TW>
 __device__ __forceinline__ void fft_fwd_from(T* v, T* sm, const TW& tw, int tau) {
     using Sh = FftShape<S, E>;
     fft_pass<S, E, k, false, NA>(v, tw, tau);
     if constexpr (k + 1 < Sh::K) {
-        fft_exchange<S, E, k, true, NA>(v, sm, tau);
-        fft_fwd_from<S, E, k + 1, NA>(v, sm, tw, tau);
+        fft_exchange<S, E, k, true, NA, CST>(v, sm, tau);
+        fft_fwd_from<S, E, k + 1, NA, CST>(v, sm, tw, tau);
     }
 }
 
-template <int S, int E, int k, int NA, class T, class TW>
+template <int S, int E, int k, int NA, int CST, class T, class TW>
 __device__ __forceinline__ void fft_inv_from(T* v, T* sm, const TW& tw, int tau) {
     fft_pass<S, E, k, true, NA>(v, tw, tau);
     if constexpr (k > 0) {
-        fft_exchange<S, E, k - 1, false, NA>(v, sm, tau);
-        fft_inv_from<S, E, k - 1, NA>(v, sm, tw, tau);
+        fft_exchange<S, E, k - 1, false, NA, CST>(v, sm, tau);
+        fft_inv_from<S, E, k - 1, NA, CST>(v, sm, tw, tau);
     }
 }
 
 // Forward FFT of NA arrays: natural layout in, spectral layout out.
-template <int S, int E, int NA = 1, class T, class TW>
+template <int S, int E, int NA = 1, int CST = 1, class T, class TW>
 __device__ __forceinline__ void fft_forward(T* v, T* sm, const TW& tw, int tau) {
-    fft_fwd_from<S, E, 0, NA>(v, sm, tw, tau);
+    fft_fwd_from<S, E, 0, NA, CST>(v, sm, tw, tau);
 }
 
 // Inverse FFT (unnormalized) of NA arrays: spectral layout in, natural layout out.
-template <int S, int E, int NA = 1, class T, class TW>
+template <int S, int E, int NA = 1, int CST = 1, class T, class TW>
 __device__ __forceinline__ void fft_inverse(T* v, T* sm, const TW& tw, int tau) {
-    fft_inv_from<S, E, FftShape<S, E>::K - 1, NA>(v, sm, tw, tau);
+    fft_inv_from<S, E, FftShape<S, E>::K - 1, NA, CST>(v, sm, tw, tau);
 }
 
 // Frequency index held by register e of thread tau in the spectral layout.

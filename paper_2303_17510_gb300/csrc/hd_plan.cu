@@ -59,6 +59,8 @@ void derive_pq(int kind, int64_t L, int64_t M, int64_t m, int64_t* p, int64_t* q
     *q = qq;
 }
 
+}  // namespace
+
 hd_status fill_axis(int dtype, int kind, int mult, int64_t L, int64_t M, int64_t m, int64_t p, int64_t q, int D,
                     AxisPlan* ax) {
     std::memset(ax, 0, sizeof(*ax));
@@ -96,7 +98,6 @@ hd_status fill_axis(int dtype, int kind, int mult, int64_t L, int64_t M, int64_t
     return HD_ERR_UNSUPPORTED;
 }
 
-}  // namespace
 
 hd_status choose_axis(int dtype, int kind, int mult, int A, int B, int64_t L, int64_t M, AxisPlan* best) {
     double best_cost = 0;
@@ -216,6 +217,7 @@ hd_status plan_create_from(hd_plan** out, const hd_desc* d, const hd_candidate* 
 }
 
 hd_status plan_create(hd_plan** out, const hd_desc* d) {
+    if (d->ndim == 2 || d->ndim == 3) return plan_create_nd(out, d);
     hd_status st = check_desc_1d(d);
     if (st != HD_OK) return st;
     if (d->m[0] == 0) {
@@ -301,9 +303,22 @@ hd_status split_execute(const hd_plan& pl, const AxisPlan& ax, int64_t count, co
     return HD_OK;
 }
 
+hd_status rows_execute(const hd_plan& pl, const AxisPlan& ax, int64_t count, const void* const* f, void* h,
+                       int64_t stride, void* scratch, cudaStream_t st) {
+    void* hh[1] = {h};
+    if (ax.path == PATH_SPLIT) return split_execute(pl, ax, count, f, hh, stride, scratch, ax.chunk, st);
+    ConvArgs a = make_conv_args(pl, ax, count, f, hh, stride);
+    return conv1d_launch(fused_cfg(pl, ax), a, st) == cudaSuccess ? HD_OK : HD_ERR_CUDA;
+}
+
 hd_status plan_execute(hd_plan* pl, int64_t count, const void* const* f, void* const* h, int64_t stride,
                        cudaStream_t st) {
     DeviceGuard g(pl->device);
+    if (pl->ndim > 1) {
+        hd_status s2 = plan_execute_nd(pl, count, f, h, stride, st);
+        if (s2 != HD_OK) pl->sticky = s2;
+        return s2;
+    }
     const AxisPlan& ax = pl->ax[0];
     if (ax.path == PATH_SPLIT) {
         hd_status s2 = split_execute(*pl, ax, count, f, h, stride, pl->scratch, ax.chunk, st);
@@ -328,6 +343,8 @@ void plan_free(hd_plan* pl) {
         if (pl->ax[i].twN) cudaFree(pl->ax[i].twN);
         if (pl->ax[i].twS2) cudaFree(pl->ax[i].twS2);
     }
+    for (int i = 0; i < 2; ++i)
+        if (pl->work[i]) cudaFree(pl->work[i]);
     if (pl->scratch) cudaFree(pl->scratch);
     cudaGetLastError();
     delete pl;

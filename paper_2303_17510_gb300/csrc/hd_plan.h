@@ -13,7 +13,7 @@
 
 namespace hd {
 
-enum { PATH_FUSED = 0, PATH_SPLIT = 1 };
+enum { PATH_FUSED = 0, PATH_SPLIT = 1, PATH_COLUMN = 2 };
 
 // One axis of a plan: the paper's parameters (m, p, q, n, D) and the
 // kernel geometry they map to (transform size S = m, p m or p m / 2;
@@ -68,6 +68,8 @@ struct hd_plan {
     int64_t instance_elems;   // stored elements of one instance (all axes)
     size_t scratch_bytes;
     void* scratch;     // split-path work buffer (chunk * A * n * S values)
+    void* work[2];     // N-D: work buffer of each outer axis level
+    int64_t inst_cap;  // N-D: outer instances per pass through the levels
     int device;
     hd_status sticky;
 };
@@ -81,6 +83,16 @@ void plan_free(hd_plan* plan);
 ConvArgs make_conv_args(const hd_plan& pl, const AxisPlan& ax, int64_t count, const void* const* f,
                         void* const* h, int64_t stride);
 Conv1dCfg fused_cfg(const hd_plan& pl, const AxisPlan& ax);
+
+hd_status fill_axis(int dtype, int kind, int mult, int64_t L, int64_t M, int64_t m, int64_t p, int64_t q, int D,
+                    AxisPlan* ax);
+// multidimensional plans (hd_nd.cu)
+hd_status plan_create_nd(hd_plan** out, const hd_desc* d);
+hd_status plan_execute_nd(hd_plan* pl, int64_t count, const void* const* f, void* const* h, int64_t stride,
+                          cudaStream_t st);
+// batched 1D convolution of rows with axis plan ax (fused or split path)
+hd_status rows_execute(const hd_plan& pl, const AxisPlan& ax, int64_t count, const void* const* f, void* h,
+                       int64_t stride, void* scratch, cudaStream_t st);
 
 // Plan for an explicit candidate (kernel variant included).
 hd_status plan_create_from(hd_plan** out, const hd_desc* d, const hd_candidate* c);
