@@ -195,6 +195,54 @@ hd_status hd_tune_cache_get(const hd_desc* d, hd_candidate* c);
 hd_status hd_tune_cache_clear(void);
 
 /* ---------------------------------------------------------------------------
+ * Ragged batches: many 1D convolutions of different L, M, A and kind in one
+ * persistent kernel launch, replayed from a CUDA graph.  (The paper computes
+ * C copies of one transform with multithreading, Section 6; a ragged batch
+ * generalizes the copies to different sizes.)  FP32, complex and centered
+ * kinds, A = 2 (product) or 3 (sum of pairwise products), B = 1.
+ * ------------------------------------------------------------------------- */
+
+/* One ragged plan for n 1D descriptions (ndim = 1 each).  Per instance,
+ * m = 0 picks parameters from the tuning cache if it holds the instance's
+ * (dtype, kind, mult, L, M), else from the learned selector if one is loaded
+ * and confident, else from the cost model.  Allocates the work buffers of the
+ * instances whose residue transforms exceed one CTA, the queue of tiles and
+ * the graph.  HD_ERR_INVALID on bad descriptions, HD_ERR_ALIASED below a
+ * dealiasing bound, HD_ERR_UNSUPPORTED when no parameters fit. */
+hd_status hd_ragged_create(hd_plan** out, int64_t n, const hd_desc* descs);
+
+/* As hd_ragged_create with the candidate of every instance given (c[i]
+ * from hd_enumerate_candidates or hd_autotune for descs[i]). */
+hd_status hd_ragged_create_candidates(hd_plan** out, int64_t n, const hd_desc* descs, const hd_candidate* c);
+
+/* Binds device buffers: f holds 3 n host-side entries, f[3 i + a] the device
+ * address of input a of instance i (entries a >= A ignored); h holds n output
+ * addresses.  Uploads the instance table (synchronously); rebinding is
+ * allowed between runs.  h[i] may equal f[3 i]. */
+hd_status hd_ragged_bind(hd_plan* plan, const void* const* f, void* const* h);
+
+/* Runs the whole ragged batch: one graph launch (a counter reset and the
+ * persistent kernel) on `stream`.  Asynchronous. */
+hd_status hd_ragged_run(const hd_plan* plan, void* stream);
+
+/* Synchronizes the stream of the last run and reports its outcome:
+ * HD_ERR_TIMEOUT if a dependency wait of the persistent kernel ran past the
+ * plan's limit (the affected tiles were skipped), HD_OK otherwise. */
+hd_status hd_ragged_status(const hd_plan* plan);
+
+/* Parameters used for instance i. */
+hd_status hd_ragged_get_params(const hd_plan* plan, int64_t i, hd_candidate* c);
+
+/* Limit of every dependency wait in the persistent kernel, in nanoseconds
+ * (default 2e9).  Re-captures the graph. */
+hd_status hd_ragged_set_wait_limit(hd_plan* plan, int64_t ns);
+
+/* Test hook: makes the row tiles of split-path instance i wait for one more
+ * column tile than exists, so that the wait runs out (HD_ERR_INVALID for an
+ * instance on the fused path). */
+hd_status hd_ragged_inject_stall(hd_plan* plan, int64_t i);
+
+/* ---------------------------------------------------------------------------
  * Allocation-free batched convolution (no counterpart in the paper).
  *
  * Some callers cannot allocate device memory when they convolve: a service

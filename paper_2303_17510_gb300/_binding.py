@@ -85,6 +85,15 @@ _sig("hd_tune_cache_put", ctypes.c_int, [ctypes.POINTER(hd_desc), ctypes.POINTER
 _sig("hd_tune_cache_get", ctypes.c_int, [ctypes.POINTER(hd_desc), ctypes.POINTER(hd_candidate)])
 _sig("hd_tune_cache_clear", ctypes.c_int, [])
 _sig("hd_convolve_batched_noalloc", ctypes.c_int, [_vp, _i64, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i64, _vp])
+_sig("hd_ragged_create", ctypes.c_int, [ctypes.POINTER(_vp), _i64, ctypes.POINTER(hd_desc)])
+_sig("hd_ragged_create_candidates", ctypes.c_int, [ctypes.POINTER(_vp), _i64, ctypes.POINTER(hd_desc),
+                                                   ctypes.POINTER(hd_candidate)])
+_sig("hd_ragged_bind", ctypes.c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp)])
+_sig("hd_ragged_run", ctypes.c_int, [_vp, _vp])
+_sig("hd_ragged_status", ctypes.c_int, [_vp])
+_sig("hd_ragged_get_params", ctypes.c_int, [_vp, _i64, ctypes.POINTER(hd_candidate)])
+_sig("hd_ragged_set_wait_limit", ctypes.c_int, [_vp, _i64])
+_sig("hd_ragged_inject_stall", ctypes.c_int, [_vp, _i64])
 
 
 def _check(rc, where):
@@ -238,6 +247,71 @@ class Plan:
 
     def forward_residue(self, f, r, out, stream=None):
         _check(lib.hd_forward_residue(self._h, _ptr(f), int(r), _ptr(out), _stream(stream)), "hd_forward_residue")
+
+    def close(self):
+        if self._h and self._h.value:
+            lib.hd_plan_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class RaggedPlan:
+    """A ragged batch of 1D convolutions run by one persistent kernel launch
+    replayed from a CUDA graph.  `descs`: list of dicts with L, M, A (2 or 3),
+    kind ("complex" or "centered") and optionally m, p, q."""
+
+    def __init__(self, descs, candidates=None):
+        n = len(descs)
+        arr = (hd_desc * n)()
+        for i, d in enumerate(descs):
+            arr[i] = make_desc(d["L"], d["M"], A=d.get("A", 2), m=d.get("m", 0), p=d.get("p", 0), q=d.get("q", 0),
+                               kind=d.get("kind", "complex"), dtype="f32")
+        self._h = _vp()
+        if candidates is None:
+            _check(lib.hd_ragged_create(ctypes.byref(self._h), n, arr), "hd_ragged_create")
+        else:
+            ca = (hd_candidate * n)(*[hd_candidate(**{k: c[k] for k, _ in hd_candidate._fields_}) for c in candidates])
+            _check(lib.hd_ragged_create_candidates(ctypes.byref(self._h), n, arr, ca), "hd_ragged_create_candidates")
+        self.n = n
+        self.descs = descs
+
+    def bind(self, fs, hs):
+        """fs[i]: list of A device arrays of instance i; hs[i]: its output."""
+        fa = (_vp * (3 * self.n))()
+        for i, row in enumerate(fs):
+            for a, x in enumerate(row):
+                fa[3 * i + a] = _ptr(x)
+        ha = (_vp * self.n)(*[_ptr(x) for x in hs])
+        _check(lib.hd_ragged_bind(self._h, fa, ha), "hd_ragged_bind")
+
+    def run(self, stream=None):
+        _check(lib.hd_ragged_run(self._h, _stream(stream)), "hd_ragged_run")
+
+    def status(self):
+        """Synchronizes the last run; returns the status name."""
+        return STATUS[lib.hd_ragged_status(self._h)]
+
+    def params(self, i):
+        c = hd_candidate()
+        _check(lib.hd_ragged_get_params(self._h, int(i), ctypes.byref(c)), "hd_ragged_get_params")
+        return c.as_dict()
+
+    def set_wait_limit(self, ns):
+        _check(lib.hd_ragged_set_wait_limit(self._h, int(ns)), "hd_ragged_set_wait_limit")
+
+    def inject_stall(self, i):
+        _check(lib.hd_ragged_inject_stall(self._h, int(i)), "hd_ragged_inject_stall")
 
     def close(self):
         if self._h and self._h.value:

@@ -347,6 +347,7 @@ hd_status hd_convolve(const hd_plan* plan, const void* const* f, void* const* h,
 hd_status hd_convolve_batched(const hd_plan* plan, int64_t count, const void* const* f, void* const* h,
                               int64_t batch_stride, void* stream) {
     if (!plan || !f || !h || count < 0) return HD_ERR_INVALID;
+    if (plan->ragged) return HD_ERR_INVALID;
     if (plan->sticky != HD_OK) return plan->sticky;
     if (count == 0) return HD_OK;
     for (int a = 0; a < plan->A; ++a)
@@ -358,7 +359,7 @@ hd_status hd_convolve_batched(const hd_plan* plan, int64_t count, const void* co
 
 hd_status hd_forward_residue(const hd_plan* plan, const void* f, int64_t r, void* outp, void* stream) {
     if (!plan || !f || !outp) return HD_ERR_INVALID;
-    if (plan->ndim != 1) return HD_ERR_INVALID;
+    if (plan->ndim != 1 || plan->ragged) return HD_ERR_INVALID;
     if (plan->sticky != HD_OK) return plan->sticky;
     const hd::AxisPlan& ax = plan->ax[0];
     if (r < 0 || r >= ax.n) return HD_ERR_INVALID;

@@ -100,27 +100,19 @@ struct ConvLaunch {
     static constexpr int MAXT = T > 256 ? T : 256;
 };
 
-// One thread group of T = S/E threads per convolution; G = blockDim.x / T
-// groups per CTA.  Shared memory per group: the A staged inputs (ls_pad
-// values each), then A padded FFT exchange buffers.  FFT twiddles are read
-// through the read-only data cache (a shared-memory table measured slower:
-// it competes with the exchanges for shared-memory bandwidth).
-// MINB: CTAs per SM the register allocation must allow (1: up to 255
-// registers for 256 threads; 2: at most 128).
-template <class R, int S, int E, int KIND, int MULT, int NB, bool COMP, int MINB>
-__global__ void __launch_bounds__(ConvLaunch<S, E>::MAXT, MINB) conv1d_kernel(const __grid_constant__ ConvArgs a) {
+// Body of one fused convolution for one thread group: instance `inst` of a,
+// thread tau of the group, the group's staging area st (A * ls_pad values)
+// and exchange buffers sm (A * SMEM values).  Every thread of the CTA runs the
+// same sequence of barriers (groups of one CTA share n).  FFT twiddles are
+// read through the read-only data cache (a shared-memory table measured
+// slower: it competes with the exchanges for shared-memory bandwidth).
+template <class R, int S, int E, int KIND, int MULT, int NB, bool COMP>
+__device__ __forceinline__ void conv1d_body(const ConvArgs& a, int64_t inst, bool valid, int tau, cplx<R>* st,
+                                            cplx<R>* sm) {
     using T = cplx<R>;
     using Sh = FftShape<S, E>;
     constexpr int TT = Sh::T;
     constexpr int A = (MULT == MULT_PRODUCT) ? 2 : 3;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int G = blockDim.x / TT;
-    const int g = threadIdx.x / TT;
-    const int tau = threadIdx.x - g * TT;
-    T* st = reinterpret_cast<T*>(smem_raw) + (size_t)g * (A * a.ls_pad + A * Sh::SMEM);
-    T* sm = st + A * a.ls_pad;
-    const int64_t inst = (int64_t)blockIdx.x * G + g;
-    const bool valid = inst < a.count;
     const T* twN = static_cast<const T*>(a.twN);
     const TwGlobal<T> twS{static_cast<const T*>(a.twS)};
 
@@ -282,6 +274,26 @@ __global__ void __launch_bounds__(ConvLaunch<S, E>::MAXT, MINB) conv1d_kernel(co
             if (j < a.Ls) hout[j] = o0;
         }
     }
+}
+
+// One thread group of T = S/E threads per convolution; G = blockDim.x / T
+// groups per CTA; shared memory per group: the A staged inputs (ls_pad values
+// each), then A padded FFT exchange buffers.  MINB: CTAs per SM the register
+// allocation must allow (1: up to 255 registers for 256 threads; 2: at most 128).
+template <class R, int S, int E, int KIND, int MULT, int NB, bool COMP, int MINB>
+__global__ void __launch_bounds__(ConvLaunch<S, E>::MAXT, MINB) conv1d_kernel(const __grid_constant__ ConvArgs a) {
+    using T = cplx<R>;
+    using Sh = FftShape<S, E>;
+    constexpr int TT = Sh::T;
+    constexpr int A = (MULT == MULT_PRODUCT) ? 2 : 3;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int G = blockDim.x / TT;
+    const int g = threadIdx.x / TT;
+    const int tau = threadIdx.x - g * TT;
+    T* st = reinterpret_cast<T*>(smem_raw) + (size_t)g * (A * a.ls_pad + A * Sh::SMEM);
+    T* sm = st + A * a.ls_pad;
+    const int64_t inst = (int64_t)blockIdx.x * G + g;
+    conv1d_body<R, S, E, KIND, MULT, NB, COMP>(a, inst, inst < a.count, tau, st, sm);
 }
 
 // Forward transform of one residue of one input, written in the paper's

@@ -338,6 +338,7 @@ void plan_free(hd_plan* pl) {
     if (!pl) return;
     DeviceGuard g(pl->device);
     cudaDeviceSynchronize();
+    if (pl->ragged) ragged_destroy(pl);
     for (int i = 0; i < 3; ++i) {
         if (pl->ax[i].twS) cudaFree(pl->ax[i].twS);
         if (pl->ax[i].twN) cudaFree(pl->ax[i].twN);

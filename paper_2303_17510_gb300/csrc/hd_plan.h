@@ -15,6 +15,8 @@ namespace hd {
 
 enum { PATH_FUSED = 0, PATH_SPLIT = 1, PATH_COLUMN = 2 };
 
+struct RaggedData;
+
 // One axis of a plan: the paper's parameters (m, p, q, n, D) and the
 // kernel geometry they map to (transform size S = m, p m or p m / 2;
 // n residues of S values; nb folded blocks).
@@ -70,6 +72,7 @@ struct hd_plan {
     void* scratch;     // split-path work buffer (chunk * A * n * S values)
     void* work[2];     // N-D: work buffer of each outer axis level
     int64_t inst_cap;  // N-D: outer instances per pass through the levels
+    hd::RaggedData* ragged;   // ragged batch plans (hd_ragged.cu)
     int device;
     hd_status sticky;
 };
@@ -86,6 +89,9 @@ Conv1dCfg fused_cfg(const hd_plan& pl, const AxisPlan& ax);
 
 hd_status fill_axis(int dtype, int kind, int mult, int64_t L, int64_t M, int64_t m, int64_t p, int64_t q, int D,
                     AxisPlan* ax);
+// ragged batch plans (hd_ragged.cu)
+hd_status ragged_create(hd_plan** out, int64_t n, const hd_desc* descs, const hd_candidate* forced);
+void ragged_destroy(hd_plan* pl);
 // multidimensional plans (hd_nd.cu)
 hd_status plan_create_nd(hd_plan** out, const hd_desc* d);
 hd_status plan_execute_nd(hd_plan* pl, int64_t count, const void* const* f, void* const* h, int64_t stride,

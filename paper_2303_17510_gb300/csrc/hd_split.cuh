@@ -46,19 +46,10 @@ __device__ __forceinline__ void dft_small(T* v) {
     dft_reg<S1, INV>(v);
 }
 
-// Forward columns: one thread per (instance, a, r, j2), j2 fastest.
+// Forward column j2 of residue r of input aa of instance inst.
 template <class R, int S1, int KIND>
-__global__ void __launch_bounds__(256) split_colfwd(const __grid_constant__ SplitArgs a) {
+__device__ __forceinline__ void split_colfwd_body(const SplitArgs& a, int64_t inst, int aa, int r, int j2) {
     using T = cplx<R>;
-    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t total = a.count * a.A * a.n * (int64_t)a.S2;
-    if (tid >= total) return;
-    const int j2 = (int)(tid % a.S2);
-    int64_t rest = tid / a.S2;
-    const int r = (int)(rest % a.n);
-    rest /= a.n;
-    const int aa = (int)(rest % a.A);
-    const int64_t inst = rest / a.A;
     const T* f = static_cast<const T*>(a.f[aa]) + inst * a.stride;
     const T* twR = static_cast<const T*>(a.twR);
     const T* twS = static_cast<const T*>(a.twS);
@@ -85,21 +76,28 @@ __global__ void __launch_bounds__(256) split_colfwd(const __grid_constant__ Spli
     }
 }
 
-// Rows: one group of S2/E threads per (instance, residue, row k1).
+// Forward columns: one thread per (instance, a, r, j2), j2 fastest.
+template <class R, int S1, int KIND>
+__global__ void __launch_bounds__(256) split_colfwd(const __grid_constant__ SplitArgs a) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t total = a.count * a.A * a.n * (int64_t)a.S2;
+    if (tid >= total) return;
+    const int j2 = (int)(tid % a.S2);
+    int64_t rest = tid / a.S2;
+    const int r = (int)(rest % a.n);
+    rest /= a.n;
+    const int aa = (int)(rest % a.A);
+    split_colfwd_body<R, S1, KIND>(a, rest / a.A, aa, r, j2);
+}
+
+// Row `row` (= (instance * n + r) * S1 + k1) for one group of S2/E threads;
+// sm is the group's A exchange buffers.
 template <class R, int S2, int E, int KIND, int MULT>
-__global__ void __launch_bounds__(ConvLaunch<S2, E>::MAXT) split_row(const __grid_constant__ SplitArgs a) {
+__device__ __forceinline__ void split_row_body(const SplitArgs& a, int64_t row, bool valid, int tau, cplx<R>* sm) {
     using T = cplx<R>;
     using Sh = FftShape<S2, E>;
     constexpr int TT = Sh::T;
     constexpr int A = (MULT == MULT_PRODUCT) ? 2 : 3;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int G = blockDim.x / TT;
-    const int g = threadIdx.x / TT;
-    const int tau = threadIdx.x - g * TT;
-    T* sm = reinterpret_cast<T*>(smem_raw) + (size_t)g * A * Sh::SMEM;
-    const int64_t row = (int64_t)blockIdx.x * G + g;
-    const int64_t rows = a.count * a.n * (int64_t)a.S1;
-    const bool valid = row < rows;
     const int k1 = (int)(row % a.S1);
     const int64_t rr = row / a.S1;
     const int r = (int)(rr % a.n);
@@ -139,15 +137,28 @@ __global__ void __launch_bounds__(ConvLaunch<S2, E>::MAXT) split_row(const __gri
     for (int e = 0; e < E; ++e) dst[tau + TT * e] = p[e];
 }
 
-// Backward columns: one thread per (instance, j2); all residues accumulated.
+// Rows: one group of S2/E threads per (instance, residue, row k1).
+template <class R, int S2, int E, int KIND, int MULT>
+__global__ void __launch_bounds__(ConvLaunch<S2, E>::MAXT) split_row(const __grid_constant__ SplitArgs a) {
+    using T = cplx<R>;
+    using Sh = FftShape<S2, E>;
+    constexpr int TT = Sh::T;
+    constexpr int A = (MULT == MULT_PRODUCT) ? 2 : 3;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int G = blockDim.x / TT;
+    const int g = threadIdx.x / TT;
+    const int tau = threadIdx.x - g * TT;
+    T* sm = reinterpret_cast<T*>(smem_raw) + (size_t)g * A * Sh::SMEM;
+    const int64_t row = (int64_t)blockIdx.x * G + g;
+    const int64_t rows = a.count * a.n * (int64_t)a.S1;
+    split_row_body<R, S2, E, KIND, MULT>(a, row, row < rows, tau, sm);
+}
+
+// Backward column j2 of instance inst; all residues accumulated.
 template <class R, int S1, int KIND, bool COMP>
-__global__ void __launch_bounds__(256) split_colbwd(const __grid_constant__ SplitArgs a) {
+__device__ __forceinline__ void split_colbwd_body(const SplitArgs& a, int64_t inst, int j2) {
     using T = cplx<R>;
     constexpr int NB = (KIND == KIND_HERMITIAN) ? 1 : 2;
-    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (tid >= a.count * (int64_t)a.S2) return;
-    const int j2 = (int)(tid % a.S2);
-    const int64_t inst = tid / a.S2;
     const T* twR = static_cast<const T*>(a.twR);
     const T* twS = static_cast<const T*>(a.twS);
     const T* base = static_cast<const T*>(a.work) + inst * a.A * (int64_t)a.n * a.S;
@@ -209,6 +220,14 @@ __global__ void __launch_bounds__(256) split_colbwd(const __grid_constant__ Spli
             if (j < a.Ls) hout[j] = o0;
         }
     }
+}
+
+// Backward columns: one thread per (instance, j2).
+template <class R, int S1, int KIND, bool COMP>
+__global__ void __launch_bounds__(256) split_colbwd(const __grid_constant__ SplitArgs a) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= a.count * (int64_t)a.S2) return;
+    split_colbwd_body<R, S1, KIND, COMP>(a, tid / a.S2, (int)(tid % a.S2));
 }
 
 }  // namespace hd
