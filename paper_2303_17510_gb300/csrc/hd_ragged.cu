@@ -155,7 +155,9 @@ size_t fused_tile_smem(int64_t S, int A, int aux) {
     return (size_t)G * fused_group_elems(S, A, aux) * 8;
 }
 
-constexpr size_t kSmemMax = 227 * 1024;
+// dynamic shared memory a ragged tile may use (the kernel's own static shared
+// memory and the per-block opt-in limit are checked at plan creation)
+constexpr size_t kSmemMax = 226 * 1024;
 
 // ragged feasibility of a candidate for one instance
 bool ragged_ok(const hd_desc* d, const hd_candidate& c) {
@@ -424,9 +426,19 @@ hd_status ragged_create(hd_plan** out, int64_t n, const hd_desc* descs, const hd
     if (st == HD_OK) st = up((void**)&rg->d_ctr, nullptr, (size_t)(2 + 2 * n) * sizeof(int));
     if (st == HD_OK) {
         // one attribute value for every ragged plan: the largest tile of any plan fits
-        if (cudaFuncSetAttribute(ragged_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax) !=
-            cudaSuccess)
+        int dev = 0, optin = 0;
+        cudaFuncAttributes fa;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (cudaFuncGetAttributes(&fa, ragged_kernel) != cudaSuccess) {
             st = HD_ERR_CUDA;
+        } else {
+            const size_t dynmax = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+            if (rg->smem > dynmax) st = HD_ERR_UNSUPPORTED;
+            else if (cudaFuncSetAttribute(ragged_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dynmax) !=
+                     cudaSuccess)
+                st = HD_ERR_CUDA;
+        }
     }
     if (st == HD_OK) {
         int dev = 0, sms = 0, per = 0;
