@@ -195,6 +195,57 @@ hd_status hd_tune_cache_get(const hd_desc* d, hd_candidate* c);
 hd_status hd_tune_cache_clear(void);
 
 /* ---------------------------------------------------------------------------
+ * Learned parameter selector (not in the paper; it stands in for the timed
+ * search of Section 6).  A small MLP predicts the log time of one convolution
+ * for a (problem, candidate) pair; an installed ensemble picks the candidate
+ * with the lowest mean prediction.  Training runs on the GPU with the
+ * library's own kernels: tanh hidden layers, a linear output, mean squared
+ * error, Adam (beta1 0.9, beta2 0.999, eps 1e-8).  FP32.
+ * ------------------------------------------------------------------------- */
+
+typedef struct hd_mlp hd_mlp;
+#define HD_SELECTOR_FEATURES 13
+
+/* Network with nlayers dense layers of sizes dims[0] -> dims[1] -> ... ->
+ * dims[nlayers] (the last must be 1); parameters start at zero. */
+hd_status hd_mlp_create(hd_mlp** out, int nlayers, const int* dims);
+/* Parameter count: for each layer W (dims[l+1] x dims[l], row-major) then b. */
+int64_t hd_mlp_num_params(const hd_mlp* m);
+/* Host <-> device copies of the parameter vector (set also resets Adam). */
+hd_status hd_mlp_set_params(hd_mlp* m, const float* host);
+hd_status hd_mlp_get_params(const hd_mlp* m, float* host);
+/* Predictions for N rows of X (device, N x dims[0] row-major) into Y (device, N). */
+hd_status hd_mlp_forward(hd_mlp* m, const float* X, int64_t N, float* Y, void* stream);
+/* Mean squared error against targets t (device, N) and its gradient (kept on
+ * the device; copied to grads_host, when non-NULL, in the parameter order).
+ * Synchronizes the stream; loss may be NULL. */
+hd_status hd_mlp_gradients(hd_mlp* m, const float* X, const float* t, int64_t N, float* loss, float* grads_host,
+                           void* stream);
+/* One Adam step with learning rate lr on the batch (X, t); loss (if non-NULL)
+ * receives the loss before the step (synchronizes the stream). */
+hd_status hd_mlp_train_step(hd_mlp* m, const float* X, const float* t, int64_t N, float lr, float* loss,
+                            void* stream);
+hd_status hd_mlp_destroy(hd_mlp* m);
+
+/* The HD_SELECTOR_FEATURES inputs of a (1D description, candidate) pair:
+ * log2 L/16, log2 M/16, L/M, A-2, centered, Hermitian, FP64, log2 S/16,
+ * log2 n/8, (n S - M)/M, split path, E/16, minb-1. */
+hd_status hd_selector_features(const hd_desc* d, const hd_candidate* c, float* out);
+
+/* Installs k trained networks (owned by the caller, kept alive while
+ * installed) as the process-wide selector used by plans with m = 0 after the
+ * tuning cache.  The ensemble is unsure about a problem when the spread (std.
+ * dev.) of its predictions for the chosen candidate exceeds sigma, or when its
+ * members disagree on the best candidate and the predicted log-time margin to
+ * the second best is below tau.  fallback = 1: an unsure choice is replaced by
+ * the timed search (hd_autotune); 0: the ensemble's choice is used anyway. */
+hd_status hd_selector_install(hd_mlp* const* models, int k, float tau, float sigma, int fallback);
+hd_status hd_selector_clear(void);
+/* The installed selector's choice for a 1D description (HD_ERR_INVALID when
+ * none is installed); *confident = 1 when the ensemble is sure. */
+hd_status hd_selector_choose(const hd_desc* d, hd_candidate* out, int* confident);
+
+/* ---------------------------------------------------------------------------
  * Ragged batches: many 1D convolutions of different L, M, A and kind in one
  * persistent kernel launch, replayed from a CUDA graph.  (The paper computes
  * C copies of one transform with multithreading, Section 6; a ragged batch

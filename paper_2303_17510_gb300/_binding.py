@@ -85,6 +85,22 @@ _sig("hd_tune_cache_put", ctypes.c_int, [ctypes.POINTER(hd_desc), ctypes.POINTER
 _sig("hd_tune_cache_get", ctypes.c_int, [ctypes.POINTER(hd_desc), ctypes.POINTER(hd_candidate)])
 _sig("hd_tune_cache_clear", ctypes.c_int, [])
 _sig("hd_convolve_batched_noalloc", ctypes.c_int, [_vp, _i64, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i64, _vp])
+_sig("hd_mlp_create", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int)])
+_sig("hd_mlp_num_params", _i64, [_vp])
+_sig("hd_mlp_set_params", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_float)])
+_sig("hd_mlp_get_params", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_float)])
+_sig("hd_mlp_forward", ctypes.c_int, [_vp, _vp, _i64, _vp, _vp])
+_sig("hd_mlp_gradients", ctypes.c_int, [_vp, _vp, _vp, _i64, ctypes.POINTER(ctypes.c_float),
+                                        ctypes.POINTER(ctypes.c_float), _vp])
+_sig("hd_mlp_train_step", ctypes.c_int, [_vp, _vp, _vp, _i64, ctypes.c_float, ctypes.POINTER(ctypes.c_float), _vp])
+_sig("hd_mlp_destroy", ctypes.c_int, [_vp])
+_sig("hd_selector_features", ctypes.c_int, [ctypes.POINTER(hd_desc), ctypes.POINTER(hd_candidate),
+                                            ctypes.POINTER(ctypes.c_float)])
+_sig("hd_selector_install", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_float, ctypes.c_float,
+                                           ctypes.c_int])
+_sig("hd_selector_clear", ctypes.c_int, [])
+_sig("hd_selector_choose", ctypes.c_int, [ctypes.POINTER(hd_desc), ctypes.POINTER(hd_candidate),
+                                          ctypes.POINTER(ctypes.c_int)])
 _sig("hd_ragged_create", ctypes.c_int, [ctypes.POINTER(_vp), _i64, ctypes.POINTER(hd_desc)])
 _sig("hd_ragged_create_candidates", ctypes.c_int, [ctypes.POINTER(_vp), _i64, ctypes.POINTER(hd_desc),
                                                    ctypes.POINTER(hd_candidate)])
@@ -329,3 +345,89 @@ class RaggedPlan:
 
     def __exit__(self, *a):
         self.close()
+
+
+SELECTOR_FEATURES = 13
+
+
+def selector_features(cand, **kw):
+    d = make_desc(**kw)
+    c = hd_candidate(**{k: cand[k] for k, _ in hd_candidate._fields_})
+    out = (ctypes.c_float * SELECTOR_FEATURES)()
+    _check(lib.hd_selector_features(ctypes.byref(d), ctypes.byref(c), out), "hd_selector_features")
+    return list(out)
+
+
+class MLP:
+    """Device MLP (tanh hidden layers, linear scalar output) trained with the
+    library's kernels.  dims: layer sizes, the last one 1."""
+
+    def __init__(self, dims):
+        self.dims = list(dims)
+        arr = (ctypes.c_int * len(dims))(*dims)
+        self._h = _vp()
+        _check(lib.hd_mlp_create(ctypes.byref(self._h), len(dims) - 1, arr), "hd_mlp_create")
+        self.nparams = int(lib.hd_mlp_num_params(self._h))
+
+    @property
+    def handle(self):
+        return self._h.value
+
+    def set_params(self, flat):
+        import numpy as np
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        assert a.size == self.nparams
+        _check(lib.hd_mlp_set_params(self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))), "hd_mlp_set_params")
+
+    def get_params(self):
+        import numpy as np
+        a = np.zeros(self.nparams, dtype=np.float32)
+        _check(lib.hd_mlp_get_params(self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))), "hd_mlp_get_params")
+        return a
+
+    def forward(self, X, Y, stream=None):
+        _check(lib.hd_mlp_forward(self._h, _ptr(X), int(X.shape[0]), _ptr(Y), _stream(stream)), "hd_mlp_forward")
+
+    def gradients(self, X, t, stream=None):
+        import numpy as np
+        g = np.zeros(self.nparams, dtype=np.float32)
+        loss = ctypes.c_float()
+        _check(lib.hd_mlp_gradients(self._h, _ptr(X), _ptr(t), int(X.shape[0]), ctypes.byref(loss),
+                                    g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), _stream(stream)),
+               "hd_mlp_gradients")
+        return float(loss.value), g
+
+    def train_step(self, X, t, lr, stream=None, want_loss=False):
+        loss = ctypes.c_float()
+        _check(lib.hd_mlp_train_step(self._h, _ptr(X), _ptr(t), int(X.shape[0]), float(lr),
+                                     ctypes.byref(loss) if want_loss else None, _stream(stream)), "hd_mlp_train_step")
+        return float(loss.value) if want_loss else None
+
+    def close(self):
+        if self._h and self._h.value:
+            lib.hd_mlp_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def selector_install(models, tau=0.05, sigma=0.25, fallback=True):
+    arr = (_vp * len(models))(*[m.handle for m in models])
+    _check(lib.hd_selector_install(arr, len(models), float(tau), float(sigma), 1 if fallback else 0),
+           "hd_selector_install")
+
+
+def selector_clear():
+    lib.hd_selector_clear()
+
+
+def selector_choose(**kw):
+    d = make_desc(**kw)
+    c = hd_candidate()
+    conf = ctypes.c_int()
+    _check(lib.hd_selector_choose(ctypes.byref(d), ctypes.byref(c), ctypes.byref(conf)), "hd_selector_choose")
+    return c.as_dict(), bool(conf.value)

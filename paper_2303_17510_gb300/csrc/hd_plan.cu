@@ -223,6 +223,16 @@ hd_status plan_create(hd_plan** out, const hd_desc* d) {
     if (d->m[0] == 0) {
         hd_candidate c;
         if (cache_lookup(d, &c) && plan_create_from(out, d, &c) == HD_OK) return HD_OK;
+        if (selector_installed()) {
+            std::vector<hd_candidate> cands;
+            enumerate_candidates(d, &cands);
+            std::vector<int> pick, conf;
+            if (!cands.empty() && selector_choose_batch({d}, {cands}, &pick, &conf) == HD_OK) {
+                c = cands[pick[0]];
+                if (!conf[0] && selector_fallback()) timed_choice(d, nullptr, &c);
+                if (plan_create_from(out, d, &c) == HD_OK) return HD_OK;
+            }
+        }
     }
     AxisPlan ax;
     if (d->m[0] == 0) st = choose_axis(d->dtype, d->kind, d->mult, d->A, d->B, d->L[0], d->M[0], &ax);

@@ -72,7 +72,17 @@ struct hd_plan {
     void* scratch;     // split-path work buffer (chunk * A * n * S values)
     void* work[2];     // N-D: work buffer of each outer axis level
     int64_t inst_cap;  // N-D: outer instances per pass through the levels
-    hd::RaggedData* ragged;   // ragged batch plans (hd_ragged.cu)
+    hd::RaggedData* ragged;   // learned selector (hd_selector.cu)
+void selector_features(const hd_desc* d, const hd_candidate* c, float* f);
+bool selector_installed();
+int selector_fallback();
+hd_status selector_choose_batch(const std::vector<const hd_desc*>& descs,
+                                const std::vector<std::vector<hd_candidate>>& cands, std::vector<int>* pick,
+                                std::vector<int>* confident);
+// timed search for one description, keeping candidates accepted by `ok`
+hd_status timed_choice(const hd_desc* d, bool (*ok)(const hd_desc*, const hd_candidate&), hd_candidate* out);
+
+// ragged batch plans (hd_ragged.cu)
     int device;
     hd_status sticky;
 };
@@ -89,6 +99,16 @@ Conv1dCfg fused_cfg(const hd_plan& pl, const AxisPlan& ax);
 
 hd_status fill_axis(int dtype, int kind, int mult, int64_t L, int64_t M, int64_t m, int64_t p, int64_t q, int D,
                     AxisPlan* ax);
+// learned selector (hd_selector.cu)
+void selector_features(const hd_desc* d, const hd_candidate* c, float* f);
+bool selector_installed();
+int selector_fallback();
+hd_status selector_choose_batch(const std::vector<const hd_desc*>& descs,
+                                const std::vector<std::vector<hd_candidate>>& cands, std::vector<int>* pick,
+                                std::vector<int>* confident);
+// timed search for one description, keeping candidates accepted by `ok`
+hd_status timed_choice(const hd_desc* d, bool (*ok)(const hd_desc*, const hd_candidate&), hd_candidate* out);
+
 // ragged batch plans (hd_ragged.cu)
 hd_status ragged_create(hd_plan** out, int64_t n, const hd_desc* descs, const hd_candidate* forced);
 void ragged_destroy(hd_plan* pl);

@@ -244,6 +244,38 @@ hd_status choose_ragged(const hd_desc* d, hd_candidate* out) {
 
 hd_status ragged_create(hd_plan** out, int64_t n, const hd_desc* descs, const hd_candidate* forced) {
     if (n <= 0 || n > (int64_t)1 << 24) return HD_ERR_INVALID;
+    // the learned selector, batched over the instances it has to choose for
+    std::vector<hd_candidate> sel(n);
+    std::vector<char> has_sel(n, 0);
+    if (!forced && selector_installed()) {
+        std::vector<const hd_desc*> ds;
+        std::vector<std::vector<hd_candidate>> cs;
+        std::vector<int64_t> idx;
+        for (int64_t i = 0; i < n; ++i) {
+            const hd_desc* d = descs + i;
+            hd_candidate tmp;
+            if (d->m[0] != 0 || d->ndim != 1 || cache_lookup(d, &tmp)) continue;
+            if (d->L[0] <= 0 || d->M[0] < hd_dealias_bound(d->kind, d->mult, d->L[0])) continue;
+            std::vector<hd_candidate> all, okc;
+            enumerate_candidates(d, &all);
+            for (auto& c : all)
+                if (ragged_ok(d, c)) okc.push_back(c);
+            if (okc.empty()) continue;
+            ds.push_back(d);
+            cs.push_back(okc);
+            idx.push_back(i);
+        }
+        std::vector<int> pick, conf;
+        if (!ds.empty() && selector_choose_batch(ds, cs, &pick, &conf) == HD_OK) {
+            const bool fb = selector_fallback() != 0;
+            for (size_t k = 0; k < ds.size(); ++k) {
+                hd_candidate c = cs[k][pick[k]];
+                if (!conf[k] && fb) timed_choice(ds[k], ragged_ok, &c);
+                sel[idx[k]] = c;
+                has_sel[idx[k]] = 1;
+            }
+        }
+    }
     RaggedData* rg = new (std::nothrow) RaggedData;
     if (!rg) return HD_ERR_NOMEM;
     rg->n = n;
@@ -268,6 +300,8 @@ hd_status ragged_create(hd_plan** out, int64_t n, const hd_desc* descs, const hd
         hd_candidate c;
         if (forced) {
             c = forced[i];
+        } else if (has_sel[i]) {
+            c = sel[i];
         } else if (d->m[0] > 0) {
             AxisPlan ax;
             hd_status s2 = fill_axis(d->dtype, d->kind, d->mult, d->L[0], d->M[0], d->m[0], d->p[0], d->q[0], 1, &ax);

@@ -166,6 +166,27 @@ bool cache_lookup(const hd_desc* d, hd_candidate* c) {
     return true;
 }
 
+// Timed search used when the selector is unsure: the batch size gives about
+// 2^21 stored values per timed call.
+hd_status timed_choice(const hd_desc* d, bool (*ok)(const hd_desc*, const hd_candidate&), hd_candidate* out) {
+    int64_t count = ((int64_t)1 << 21) / std::max<int64_t>(d->L[0], 64);
+    count = std::max<int64_t>(1, std::min<int64_t>(count, 4096));
+    std::vector<hd_candidate> all(256);
+    int n = 0;
+    hd_candidate best;
+    hd_status st = hd_autotune(d, count, 3, all.data(), (int)all.size(), &n, &best);
+    if (st != HD_OK) return st;
+    bool found = false;
+    for (int i = 0; i < n && i < (int)all.size(); ++i) {
+        if (all[i].ms <= 0 || (ok && !ok(d, all[i]))) continue;
+        if (!found || all[i].ms < out->ms) {
+            *out = all[i];
+            found = true;
+        }
+    }
+    return found ? HD_OK : HD_ERR_UNSUPPORTED;
+}
+
 }  // namespace hd
 
 using namespace hd;
