@@ -173,11 +173,12 @@ hd_status plan_finish(const hd_desc* d, const AxisPlan& ax, hd_plan** out) {
         if (st == HD_OK) st = upload_fft_twiddles(a0.S2, a0.E, d->dtype, &a0.twS2);
         if (st == HD_OK) {
             // work buffer of Section 5: A n S values per instance, a chunk of
-            // instances at a time (up to 64 instances or 128 MiB)
+            // instances at a time, at most 64 MiB so that the round trips
+            // between the three phases stay in L2
             const size_t esz = d->dtype == HD_F64 ? 16 : 8;
             const size_t per = (size_t)d->A * (size_t)a0.n * (size_t)a0.S * esz;
-            int64_t ch = (int64_t)((128u << 20) / per);
-            if (ch > 64) ch = 64;
+            int64_t ch = (int64_t)((64u << 20) / per);
+            if (ch > 2048) ch = 2048;
             if (ch < 1) ch = 1;
             a0.chunk = ch;
             pl->scratch_bytes = per * (size_t)ch;

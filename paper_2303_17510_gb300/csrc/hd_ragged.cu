@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <new>
@@ -20,7 +21,10 @@ namespace {
 constexpr int RT_THREADS = 256;
 constexpr int kRowS2 = 4096;   // split rows of the ragged kernel: size-4096 FFTs, 16 values per thread
 constexpr int kRowE = 16;
-constexpr int kColBlk = 256;   // columns per COLFWD / COLBWD tile
+// columns per COLFWD / COLBWD tile: about 16 K elements (column x S1), so that
+// the per-tile cost (queue atomic, barriers, dependency counters) is spread
+// over enough independent loads per thread
+__host__ __device__ constexpr int col_blk(int S1) { return S1 <= 4 ? 4096 : 16384 / S1; }
 
 __host__ __device__ constexpr int ragged_E(int S) { return S <= 2048 ? (S < 8 ? S : 8) : 16; }
 
@@ -44,15 +48,22 @@ __device__ __noinline__ void fused_tile(const RaggedArgs& ra, const RTile& t, un
     conv1d_body<float, S, E, KIND, MULT, NB, true>(a, 0, valid, tau, st, sm);
 }
 
+// columns a thread handles together in the column phases (loads in flight)
+__host__ __device__ constexpr int col_u(int S1) { return S1 >= 16 ? 1 : 16 / S1 > 8 ? 8 : 16 / S1; }
+
 template <int S1, int KIND>
 __device__ __noinline__ void colfwd_tile(const RaggedArgs& ra, const RTile& t) {
     const RInst& r = ra.inst[t.first];
     const SplitArgs a = split_args_of(r);
-    const int nblk = r.S2 / kColBlk;
+    constexpr int CB = col_blk(S1);
+    constexpr int U = col_u(S1);
+    static_assert(CB % (RT_THREADS * U) == 0, "column tile");
+    const int nblk = r.S2 / CB;
     const int blk = t.count % nblk;
     const int rr = (t.count / nblk) % r.n;
     const int aa = t.count / nblk / r.n;
-    split_colfwd_body<float, S1, KIND>(a, 0, aa, rr, blk * kColBlk + (int)threadIdx.x);
+    for (int c = (int)threadIdx.x; c < CB; c += RT_THREADS * U)
+        split_colfwd_multi<float, S1, KIND, U>(a, 0, aa, rr, blk * CB + c, RT_THREADS);
 }
 
 template <int KIND, int MULT>
@@ -67,7 +78,11 @@ template <int S1, int KIND>
 __device__ __noinline__ void colbwd_tile(const RaggedArgs& ra, const RTile& t) {
     const RInst& r = ra.inst[t.first];
     const SplitArgs a = split_args_of(r);
-    split_colbwd_body<float, S1, KIND, true>(a, 0, t.count * kColBlk + (int)threadIdx.x);
+    constexpr int CB = col_blk(S1);
+    constexpr int U = col_u(S1) > 4 ? 4 : col_u(S1);
+    static_assert(CB % (RT_THREADS * U) == 0, "column tile");
+    for (int c = (int)threadIdx.x; c < CB; c += RT_THREADS * U)
+        split_colbwd_multi<float, S1, KIND, true, U>(a, 0, t.count * CB + c, RT_THREADS);
 }
 
 // configuration id of a FUSED tile
@@ -87,49 +102,62 @@ __device__ void run_fused(const RaggedArgs& ra, const RTile& t, unsigned char* s
     }
 }
 
+// A wait that runs out records HD_ERR_TIMEOUT and skips the tile's work, but
+// the tile still signals its counter, so dependents wait at most once more.
 __device__ void run_split(const RaggedArgs& ra, const RTile& t, unsigned char* smem, int* flag) {
     const RInst& r = ra.inst[t.first];
     const int kind = r.H >= 0 ? KIND_CENTERED : KIND_COMPLEX;   // H < 0 marks complex data
     if (t.type == RT_COLFWD) {
+        if (r.gneed <= 0 || cta_wait(ra.gdone + r.gprev, r.gneed, ra, flag)) {
 #define HD_CF(S1)                                                                          \
     case S1:                                                                               \
         if (kind == KIND_COMPLEX) colfwd_tile<S1, KIND_COMPLEX>(ra, t);                    \
         else colfwd_tile<S1, KIND_CENTERED>(ra, t);                                        \
         break;
-        switch (r.S1) { HD_CF(2) HD_CF(4) HD_CF(8) HD_CF(16) default: break; }
+            switch (r.S1) { HD_CF(2) HD_CF(4) HD_CF(8) HD_CF(16) default: break; }
 #undef HD_CF
+        }
         cta_signal(ra.cnt1 + t.first);
     } else if (t.type == RT_ROW) {
-        if (!cta_wait(ra.cnt1 + t.first, r.ncf + r.stall, ra, flag)) return;
-        if (r.A == 2) {
-            if (kind == KIND_COMPLEX) row_tile<KIND_COMPLEX, MULT_PRODUCT>(ra, t, smem);
-            else row_tile<KIND_CENTERED, MULT_PRODUCT>(ra, t, smem);
-        } else {
-            if (kind == KIND_COMPLEX) row_tile<KIND_COMPLEX, MULT_PAIRS3>(ra, t, smem);
-            else row_tile<KIND_CENTERED, MULT_PAIRS3>(ra, t, smem);
+        if (cta_wait(ra.cnt1 + t.first, r.ncf + r.stall, ra, flag)) {
+            if (r.A == 2) {
+                if (kind == KIND_COMPLEX) row_tile<KIND_COMPLEX, MULT_PRODUCT>(ra, t, smem);
+                else row_tile<KIND_CENTERED, MULT_PRODUCT>(ra, t, smem);
+            } else {
+                if (kind == KIND_COMPLEX) row_tile<KIND_COMPLEX, MULT_PAIRS3>(ra, t, smem);
+                else row_tile<KIND_CENTERED, MULT_PAIRS3>(ra, t, smem);
+            }
         }
         cta_signal(ra.cnt2 + t.first);
     } else {
-        if (!cta_wait(ra.cnt2 + t.first, r.nrow, ra, flag)) return;
+        if (cta_wait(ra.cnt2 + t.first, r.nrow, ra, flag)) {
 #define HD_CB(S1)                                                                          \
     case S1:                                                                               \
         if (kind == KIND_COMPLEX) colbwd_tile<S1, KIND_COMPLEX>(ra, t);                    \
         else colbwd_tile<S1, KIND_CENTERED>(ra, t);                                        \
         break;
-        switch (r.S1) { HD_CB(2) HD_CB(4) HD_CB(8) HD_CB(16) default: break; }
+            switch (r.S1) { HD_CB(2) HD_CB(4) HD_CB(8) HD_CB(16) default: break; }
 #undef HD_CB
+        }
+        cta_signal(ra.gdone + r.grp);
     }
 }
 
+// Persistent loop.  Thread 0 claims the next tile while the CTA works on the
+// current one, so the queue atomic is off the critical path.  A claimed tile
+// only waits on earlier tiles, and the earliest unfinished tile is always
+// some CTA's current tile (or the next of a CTA whose current one finished),
+// so the queue always drains.
 __global__ void __launch_bounds__(RT_THREADS, 1) ragged_kernel(const __grid_constant__ RaggedArgs ra) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_tile, s_flag;
+    __shared__ int s_next, s_flag;
+    if (threadIdx.x == 0) s_next = atomicAdd(ra.head, 1);
+    __syncthreads();
     for (;;) {
-        if (threadIdx.x == 0) s_tile = atomicAdd(ra.head, 1);
-        __syncthreads();
-        const int ti = s_tile;
+        const int ti = s_next;
         __syncthreads();
         if (ti >= ra.ntiles) return;
+        if (threadIdx.x == 0) s_next = atomicAdd(ra.head, 1);
         const RTile t = ra.tiles[ti];
         if (t.type == RT_FUSED) run_fused(ra, t, smem);
         else run_split(ra, t, smem, &s_flag);
@@ -159,6 +187,21 @@ size_t fused_tile_smem(int64_t S, int A, int aux) {
 // memory and the per-block opt-in limit are checked at plan creation)
 constexpr size_t kSmemMax = 226 * 1024;
 
+// split work buffers: groups of at most kGroupBytes in a ring of kRing buffers
+// (ring >= 3 keeps every wait pointing to an earlier stage of the queue)
+constexpr size_t kGroupBytes = 16u << 20;
+constexpr int kRing = 4;
+
+// group size in bytes; HD_RAGGED_GROUP_MB overrides the default (tuning)
+size_t group_bytes() {
+    const char* e = std::getenv("HD_RAGGED_GROUP_MB");
+    if (e && *e) {
+        const long v = std::strtol(e, nullptr, 10);
+        if (v >= 1 && v <= 4096) return (size_t)v << 20;
+    }
+    return kGroupBytes;
+}
+
 // ragged feasibility of a candidate for one instance
 bool ragged_ok(const hd_desc* d, const hd_candidate& c) {
     const int64_t Ls = d->L[0];
@@ -181,7 +224,8 @@ struct RaggedData {
     RInst* d_inst = nullptr;
     RTile* d_tiles = nullptr;
     int* d_order = nullptr;
-    int* d_ctr = nullptr;              // head, err, cnt1[n], cnt2[n]
+    int* d_ctr = nullptr;              // head, err, cnt1[n], cnt2[n], gdone[ngroups]
+    int ngroups = 0;                   // split work-buffer groups
     void* d_work = nullptr;
     std::map<std::tuple<int64_t, int>, void*> fft_tab;
     std::map<std::tuple<int64_t, int64_t>, void*> twist_tab;
@@ -284,7 +328,6 @@ hd_status ragged_create(hd_plan** out, int64_t n, const hd_desc* descs, const hd
     rg->kinds.resize(n);
     hd_status st = HD_OK;
     size_t work_total = 0;
-    std::vector<size_t> work_off(n, (size_t)-1);
     for (int64_t i = 0; i < n && st == HD_OK; ++i) {
         const hd_desc* d = descs + i;
         if (d->ndim != 1 || d->dtype != HD_F32 || d->B != 1 || (d->kind != HD_COMPLEX && d->kind != HD_CENTERED) ||
@@ -343,10 +386,9 @@ hd_status ragged_create(hd_plan** out, int64_t n, const hd_desc* descs, const hd
         if (c.S > 4096) {
             r.S2 = kRowS2;
             r.S1 = (int)(c.S / kRowS2);
-            r.ncf = d->A * r.n * (kRowS2 / kColBlk);
+            r.ncf = d->A * r.n * (kRowS2 / col_blk(r.S1));
+            r.ncb = kRowS2 / col_blk(r.S1);
             r.nrow = r.n * r.S1;
-            work_off[i] = work_total;
-            work_total += (size_t)d->A * (size_t)c.n * (size_t)c.S * 8;
         }
     }
     if (st != HD_OK) {
@@ -385,29 +427,74 @@ hd_status ragged_create(hd_plan** out, int64_t n, const hd_desc* descs, const hd
             r.twS = rg->fft_tab[kf];
         }
     }
-    if (st == HD_OK && work_total > 0) {
+    // Split instances, largest work buffer first, packed into groups of at most
+    // kGroupBytes; group g uses buffer g mod kRing of a ring whose total stays
+    // within L2, so the work-buffer round trips between the three phases are
+    // served by L2 rather than HBM.
+    std::vector<int> split_ids;
+    for (int64_t i = 0; i < n; ++i)
+        if (rg->inst[i].S > 4096) split_ids.push_back((int)i);
+    auto work_of = [&](int i) { return (size_t)rg->inst[i].A * (size_t)rg->inst[i].n * (size_t)rg->inst[i].S * 8; };
+    std::stable_sort(split_ids.begin(), split_ids.end(), [&](int x, int y) { return work_of(x) > work_of(y); });
+    std::vector<std::vector<int>> sgroups;
+    size_t buf = 0;
+    {
+        const size_t gb = group_bytes();
+        size_t used = 0;
+        for (int i : split_ids) {
+            const size_t w = work_of(i);
+            if (sgroups.empty() || used + w > gb) {
+                sgroups.emplace_back();
+                used = 0;
+            }
+            sgroups.back().push_back(i);
+            used += w;
+            buf = std::max(buf, used);
+        }
+    }
+    const int ng = (int)sgroups.size();
+    rg->ngroups = ng;
+    if (st == HD_OK && ng > 0) {
+        const int ring = std::min(ng, kRing);
+        work_total = buf * (size_t)ring;
         if (cudaMalloc(&rg->d_work, work_total) != cudaSuccess) {
             cudaGetLastError();
             st = HD_ERR_NOMEM;
         } else {
-            for (int64_t i = 0; i < n; ++i)
-                if (work_off[i] != (size_t)-1) rg->inst[i].work = static_cast<char*>(rg->d_work) + work_off[i];
+            for (int g = 0; g < ng; ++g) {
+                size_t off = (size_t)(g % ring) * buf;
+                for (int i : sgroups[g]) {
+                    RInst& r = rg->inst[i];
+                    r.work = static_cast<char*>(rg->d_work) + off;
+                    off += work_of(i);
+                    r.grp = g;
+                    r.gprev = g >= ring ? g - ring : 0;
+                    r.gneed = 0;
+                }
+            }
+            // the COLFWD tiles of group g wait for all COLBWD tiles of group g - ring
+            for (int g = ring; g < ng; ++g) {
+                int ncb = 0;
+                for (int i : sgroups[g - ring]) ncb += rg->inst[i].ncb;
+                for (int i : sgroups[g]) rg->inst[i].gneed = ncb;
+            }
         }
     }
     if (st != HD_OK) {
         ragged_free(rg);
         return st;
     }
-    // work queue: COLFWD of every split instance, FUSED tiles by decreasing cost, then ROW, then COLBWD
-    std::vector<RTile> colf, rows, colb, fused;
+    // Work queue in stages s = 0 .. ng + 1: stage s holds COLFWD of group s,
+    // ROW of group s - 1 and COLBWD of group s - 2, followed by an equal share
+    // of the FUSED tiles (by decreasing cost).  Every wait points to an
+    // earlier stage: ROW(g) and COLBWD(g) to stage g and g + 1, COLFWD(g) to
+    // COLBWD(g - ring) in stage g - ring + 2 < g for ring >= 3.
+    std::vector<RTile> fused;
     size_t smem = 0;
     std::map<std::tuple<int, int>, std::vector<int>> groups;   // (cfg, n) -> instances
     for (int64_t i = 0; i < n; ++i) {
         const RInst& r = rg->inst[i];
         if (r.S > 4096) {
-            for (int c = 0; c < r.ncf; ++c) colf.push_back(RTile{RT_COLFWD, 0, (int)i, c, 0, 0, 0, 0});
-            for (int c = 0; c < r.nrow; ++c) rows.push_back(RTile{RT_ROW, 0, (int)i, c, 0, 0, 0, 0});
-            for (int c = 0; c < r.S2 / kColBlk; ++c) colb.push_back(RTile{RT_COLBWD, 0, (int)i, c, 0, 0, 0, 0});
             smem = std::max(smem, (size_t)r.A * (kRowS2 + kRowS2 / 16) * 8);
         } else {
             const int kindnb = rg->kinds[i] == HD_CENTERED ? 2 : (r.L > r.S ? 1 : 0);
@@ -435,10 +522,24 @@ hd_status ragged_create(hd_plan** out, int64_t n, const hd_desc* descs, const hd
     }
     std::stable_sort(ft.begin(), ft.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
     for (auto& x : ft) fused.push_back(x.second);
-    rg->tiles = colf;
-    rg->tiles.insert(rg->tiles.end(), fused.begin(), fused.end());
-    rg->tiles.insert(rg->tiles.end(), rows.begin(), rows.end());
-    rg->tiles.insert(rg->tiles.end(), colb.begin(), colb.end());
+    rg->tiles.clear();
+    const int nstage = ng > 0 ? ng + 2 : 0;
+    size_t fpos = 0;
+    for (int sg = 0; sg < nstage; ++sg) {
+        if (sg < ng)
+            for (int i : sgroups[sg])
+                for (int c = 0; c < rg->inst[i].ncf; ++c) rg->tiles.push_back(RTile{RT_COLFWD, 0, i, c, 0, 0, 0, 0});
+        if (sg >= 1 && sg - 1 < ng)
+            for (int i : sgroups[sg - 1])
+                for (int c = 0; c < rg->inst[i].nrow; ++c) rg->tiles.push_back(RTile{RT_ROW, 0, i, c, 0, 0, 0, 0});
+        if (sg >= 2)
+            for (int i : sgroups[sg - 2])
+                for (int c = 0; c < rg->inst[i].ncb; ++c)
+                    rg->tiles.push_back(RTile{RT_COLBWD, 0, i, c, 0, 0, 0, 0});
+        const size_t upto = fused.size() * (size_t)(sg + 1) / (size_t)(nstage + 1);
+        for (; fpos < upto; ++fpos) rg->tiles.push_back(fused[fpos]);
+    }
+    for (; fpos < fused.size(); ++fpos) rg->tiles.push_back(fused[fpos]);
     rg->smem = smem;
     if (smem > kSmemMax) {
         ragged_free(rg);
@@ -457,7 +558,7 @@ hd_status ragged_create(hd_plan** out, int64_t n, const hd_desc* descs, const hd
     st = up((void**)&rg->d_tiles, rg->tiles.data(), rg->tiles.size() * sizeof(RTile));
     if (st == HD_OK) st = up((void**)&rg->d_order, rg->order.data(), rg->order.size() * sizeof(int));
     if (st == HD_OK) st = up((void**)&rg->d_inst, rg->inst.data(), rg->inst.size() * sizeof(RInst));
-    if (st == HD_OK) st = up((void**)&rg->d_ctr, nullptr, (size_t)(2 + 2 * n) * sizeof(int));
+    if (st == HD_OK) st = up((void**)&rg->d_ctr, nullptr, (size_t)(2 + 2 * n + ng) * sizeof(int));
     if (st == HD_OK) {
         // one attribute value for every ragged plan: the largest tile of any plan fits
         int dev = 0, optin = 0;
@@ -524,9 +625,10 @@ hd_status capture(RaggedData* rg) {
     ra.err = rg->d_ctr + 1;
     ra.cnt1 = rg->d_ctr + 2;
     ra.cnt2 = rg->d_ctr + 2 + rg->n;
+    ra.gdone = rg->d_ctr + 2 + 2 * rg->n;
     ra.wait_ns = rg->wait_ns;
     if (cudaStreamBeginCapture(rg->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return HD_ERR_CUDA;
-    cudaMemsetAsync(rg->d_ctr, 0, (size_t)(2 + 2 * rg->n) * sizeof(int), rg->cap);
+    cudaMemsetAsync(rg->d_ctr, 0, (size_t)(2 + 2 * rg->n + rg->ngroups) * sizeof(int), rg->cap);
     ragged_kernel<<<rg->grid, RT_THREADS, rg->smem, rg->cap>>>(ra);
     cudaError_t e = cudaStreamEndCapture(rg->cap, &rg->graph);
     if (e != cudaSuccess) return HD_ERR_CUDA;

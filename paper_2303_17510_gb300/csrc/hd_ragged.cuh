@@ -7,13 +7,17 @@
 //            blocks, mult, residue count), one thread group each (the fused
 //            residue-at-a-time body of hd_conv1d.cuh);
 //   COLFWD, ROW, COLBWD : the three phases of the split path (hd_split.cuh) for
-//            one large instance, 256 columns or one row per tile.
+//            one large instance, a block of columns or one row per tile.
 // A split instance's ROW tiles wait for all its COLFWD tiles, its COLBWD tiles
 // for all its ROW tiles, through per-instance counters (release by the
-// producer, acquire by the consumer).  Every consumer is queued after all of
-// its producers, and a dequeued producer never waits on a later tile, so the
-// waits always end; they are still bounded in time: a wait that exceeds the
-// plan's limit records HD_ERR_TIMEOUT in an error word and skips its tile.
+// producer, acquire by the consumer).  Split instances are packed into groups
+// whose work buffers (A n S values each) share a small ring of buffers sized
+// to stay in L2; the COLFWD tiles of group g wait until every COLBWD tile of
+// group g - ring has finished with the buffer (a per-group counter).  Every
+// consumer is queued after all of its producers, and a dequeued producer never
+// waits on a later tile, so the waits always end; they are still bounded in
+// time: a wait that exceeds the plan's limit records HD_ERR_TIMEOUT in an
+// error word and skips its tile.
 #pragma once
 
 #include "hd_split.cuh"
@@ -32,7 +36,9 @@ struct RInst {
     void* work;          // split: A n S values
     double invN;
     int L, Ls, H, n, N, S, S1, S2, A, ls_pad;
-    int ncf, nrow;       // split: number of COLFWD / ROW tiles (dependency targets)
+    int ncf, nrow, ncb;  // split: number of COLFWD / ROW / COLBWD tiles
+    int grp;             // split: work-buffer group
+    int gprev, gneed;    // split: group whose COLBWD tiles free the buffer, and their number (0: none)
     int stall;           // test hook: an extra, never-satisfied dependency
 };
 
@@ -53,6 +59,7 @@ struct RaggedArgs {
     int* head;             // queue position
     int* cnt1;             // per instance: finished COLFWD tiles
     int* cnt2;             // per instance: finished ROW tiles
+    int* gdone;            // per split group: finished COLBWD tiles
     int* err;              // HD_ERR_TIMEOUT on a wait that ran out
     long long wait_ns;     // wait limit
 };

@@ -76,6 +76,47 @@ __device__ __forceinline__ void split_colfwd_body(const SplitArgs& a, int64_t in
     }
 }
 
+// U columns j2 = j2base + u * jstep of one (instance, input, residue) by one
+// thread: every load of the U columns is issued before the first store, so a
+// thread keeps U * S1 loads in flight (the persistent ragged kernel runs one
+// CTA per SM and relies on this for latency hiding).
+template <class R, int S1, int KIND, int U>
+__device__ __forceinline__ void split_colfwd_multi(const SplitArgs& a, int64_t inst, int aa, int r, int j2base,
+                                                   int jstep) {
+    using T = cplx<R>;
+    const T* f = static_cast<const T*>(a.f[aa]) + inst * a.stride;
+    const T* twR = static_cast<const T*>(a.twR);
+    const T* twS = static_cast<const T*>(a.twS);
+    ConvArgs ca;
+    ca.L = a.L;
+    ca.Ls = a.Ls;
+    ca.H = a.H;
+    T cr = ldtw(twR + (int64_t)a.n * a.S + r);      // zeta_N^{r S}
+    if constexpr (KIND != KIND_COMPLEX) cr = cconj(cr);
+    T v[U][S1];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+#pragma unroll
+        for (int j1 = 0; j1 < S1; ++j1) {
+            const int j = j1 * a.S2 + j2base + u * jstep;
+            T b0, b1;
+            load_fold<KIND>(f, j, a.S, ca, true, b0, b1);
+            v[u][j1] = cmul(cadd(b0, cmul(cr, b1)), ldtw(twR + (int64_t)r * a.S + j));
+        }
+    }
+    T* w = static_cast<T*>(a.work) + ((inst * a.A + aa) * a.n + r) * (int64_t)a.S;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int j2 = j2base + u * jstep;
+        dft_small<S1, false>(v[u]);
+#pragma unroll
+        for (int k1 = 0; k1 < S1; ++k1) {
+            const T t = k1 == 0 ? v[u][0] : cmul(v[u][k1], ldtw(twS + k1 * a.S2 + j2));
+            w[(int64_t)k1 * a.S2 + j2] = t;
+        }
+    }
+}
+
 // Forward columns: one thread per (instance, a, r, j2), j2 fastest.
 template <class R, int S1, int KIND>
 __global__ void __launch_bounds__(256) split_colfwd(const __grid_constant__ SplitArgs a) {
@@ -218,6 +259,88 @@ __device__ __forceinline__ void split_colbwd_body(const SplitArgs& a, int64_t in
             if (j >= a.S - a.H) hout[j - a.S + a.H] = o1;
         } else {
             if (j < a.Ls) hout[j] = o0;
+        }
+    }
+}
+
+// U columns j2 = j2base + u * jstep of one instance by one thread, all
+// residues: per residue the U * S1 work-buffer loads are issued together.
+template <class R, int S1, int KIND, bool COMP, int U>
+__device__ __forceinline__ void split_colbwd_multi(const SplitArgs& a, int64_t inst, int j2base, int jstep) {
+    using T = cplx<R>;
+    constexpr int NB = (KIND == KIND_HERMITIAN) ? 1 : 2;
+    constexpr int NA = 2 * S1;
+    const T* twR = static_cast<const T*>(a.twR);
+    const T* twS = static_cast<const T*>(a.twS);
+    const T* base = static_cast<const T*>(a.work) + inst * a.A * (int64_t)a.n * a.S;
+    R s0[U][NA], c0[U][COMP ? NA : 1], s1[U][NB == 2 ? NA : 1], c1[U][(NB == 2 && COMP) ? NA : 1];
+    R dummy = 0;
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int i = 0; i < NA; ++i) {
+            s0[u][i] = 0;
+            if constexpr (COMP) c0[u][i] = 0;
+            if constexpr (NB == 2) {
+                s1[u][i] = 0;
+                if constexpr (COMP) c1[u][i] = 0;
+            }
+        }
+    for (int r = 0; r < a.n; ++r) {
+        T cr = ldtw(twR + (int64_t)a.n * a.S + r);
+        if constexpr (KIND != KIND_COMPLEX) cr = cconj(cr);
+        T v[U][S1];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int k1 = 0; k1 < S1; ++k1)
+                v[u][k1] = base[(int64_t)r * a.S + (int64_t)k1 * a.S2 + j2base + u * jstep];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int j2 = j2base + u * jstep;
+#pragma unroll
+            for (int k1 = 1; k1 < S1; ++k1) v[u][k1] = cmulc(v[u][k1], ldtw(twS + k1 * a.S2 + j2));
+            dft_small<S1, true>(v[u]);
+#pragma unroll
+            for (int j1 = 0; j1 < S1; ++j1) {
+                const int j = j1 * a.S2 + j2;
+                T y = cmulc(v[u][j1], ldtw(twR + (int64_t)r * a.S + j));
+                acc_add<R, COMP>(s0[u][2 * j1], COMP ? c0[u][2 * j1] : dummy, y.x);
+                acc_add<R, COMP>(s0[u][2 * j1 + 1], COMP ? c0[u][2 * j1 + 1] : dummy, y.y);
+                if constexpr (NB == 2) {
+                    const T y1 = cmulc(y, cr);
+                    acc_add<R, COMP>(s1[u][2 * j1], COMP ? c1[u][2 * j1] : dummy, y1.x);
+                    acc_add<R, COMP>(s1[u][2 * j1 + 1], COMP ? c1[u][2 * j1 + 1] : dummy, y1.y);
+                }
+            }
+        }
+    }
+    T* hout = static_cast<T*>(a.h) + inst * a.stride;
+    const R sc = R(a.invN);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int j2 = j2base + u * jstep;
+#pragma unroll
+        for (int j1 = 0; j1 < S1; ++j1) {
+            const int j = j1 * a.S2 + j2;
+            const R x0 = COMP ? s0[u][2 * j1] + c0[u][2 * j1] : s0[u][2 * j1];
+            const R y0 = COMP ? s0[u][2 * j1 + 1] + c0[u][2 * j1 + 1] : s0[u][2 * j1 + 1];
+            const T o0 = mk<T>(x0 * sc, y0 * sc);
+            T o1 = czero<T>();
+            if constexpr (NB == 2) {
+                const R x1 = COMP ? s1[u][2 * j1] + c1[u][2 * j1] : s1[u][2 * j1];
+                const R y1 = COMP ? s1[u][2 * j1 + 1] + c1[u][2 * j1 + 1] : s1[u][2 * j1 + 1];
+                o1 = mk<T>(x1 * sc, y1 * sc);
+            }
+            if constexpr (KIND == KIND_COMPLEX) {
+                if (j < a.L) hout[j] = o0;
+                if (j + a.S < a.L) hout[j + a.S] = o1;
+            } else if constexpr (KIND == KIND_CENTERED) {
+                if (j < a.L - a.H) hout[j + a.H] = o0;
+                if (j >= a.S - a.H) hout[j - a.S + a.H] = o1;
+            } else {
+                if (j < a.Ls) hout[j] = o0;
+            }
         }
     }
 }
