@@ -122,7 +122,7 @@ __device__ __forceinline__ void conv1d_body(const ConvArgs& a, int64_t inst, boo
         for (int aa = 0; aa < A; ++aa) {
             const T* src = static_cast<const T*>(a.f[aa]) + inst * a.stride;
             T* dst = st + aa * a.ls_pad;
-            for (int i = tau; i < a.Ls; i += TT) dst[i] = src[i];
+            for (int i = tau; i < a.Ls; i += TT) dst[i] = __ldcs(src + i);   // streamed: keep L1 for the tables
         }
     }
     __syncthreads();
@@ -157,9 +157,15 @@ __device__ __forceinline__ void conv1d_body(const ConvArgs& a, int64_t inst, boo
                 const T tw = ldtw(twr + j);
 #pragma unroll
                 for (int aa = 0; aa < A; ++aa) {
-                    T b0, b1;
-                    load_fold<KIND>(st + aa * a.ls_pad, j, S, a, valid, b0, b1);
-                    v[aa * E + e] = cmul(cadd(b0, cmul(cr, b1)), tw);
+                    if constexpr (KIND == KIND_COMPLEX && NB == 1) {
+                        // L <= S: one block, nothing folds in
+                        const T* sa = st + aa * a.ls_pad;
+                        v[aa * E + e] = (valid && j < a.L) ? cmul(sa[j], tw) : czero<T>();
+                    } else {
+                        T b0, b1;
+                        load_fold<KIND>(st + aa * a.ls_pad, j, S, a, valid, b0, b1);
+                        v[aa * E + e] = cmul(cadd(b0, cmul(cr, b1)), tw);
+                    }
                 }
             }
             fft_forward<S, E, A>(v, sm, twS, tau);
@@ -261,17 +267,17 @@ __device__ __forceinline__ void conv1d_body(const ConvArgs& a, int64_t inst, boo
             o1 = mk<T>(x1 * sc, y1 * sc);
         }
         if constexpr (KIND == KIND_COMPLEX) {
-            if (j < a.L) hout[j] = o0;
+            if (j < a.L) __stcs(hout + j, o0);
             if constexpr (NB == 2) {
-                if (j + S < a.L) hout[j + S] = o1;
+                if (j + S < a.L) __stcs(hout + j + S, o1);
             }
         } else if constexpr (KIND == KIND_CENTERED) {
-            if (j < a.L - a.H) hout[j + a.H] = o0;
+            if (j < a.L - a.H) __stcs(hout + j + a.H, o0);
             if constexpr (NB == 2) {
-                if (j >= S - a.H) hout[j - S + a.H] = o1;
+                if (j >= S - a.H) __stcs(hout + j - S + a.H, o1);
             }
         } else {
-            if (j < a.Ls) hout[j] = o0;
+            if (j < a.Ls) __stcs(hout + j, o0);
         }
     }
 }

@@ -12,9 +12,15 @@
 namespace hd {
 
 // FP32 residue sums are compensated unless HD_COMP=0 is set in the environment.
-bool comp_default() {
+// Compensated (TwoSum) accumulation of the residue contributions pays when
+// many residues are summed: the plain FP32 sum of n terms errs by at most
+// (n - 1) u relative to the sum of magnitudes, below the O(u log2 S) error of
+// the FFTs themselves for n < 8.  HD_COMP=1 / HD_COMP=0 forces it on / off.
+bool comp_default(int64_t n) {
     const char* e = std::getenv("HD_COMP");
-    return !(e && e[0] == '0');
+    if (e && e[0] == '0') return false;
+    if (e && e[0] == '1') return true;
+    return n >= 8;
 }
 
 namespace {
@@ -81,7 +87,7 @@ hd_status fill_axis(int dtype, int kind, int mult, int64_t L, int64_t M, int64_t
     ax->D = D <= 0 ? 1 : D;
     ax->nb = nb;
     ax->E = S < 8 ? (int)S : 8;
-    ax->comp = dtype == HD_F32 && comp_default();
+    ax->comp = dtype == HD_F32 && comp_default(n);
     ax->minb = default_minb(dtype, S);
     if (fused_supported(dtype, kind, mult, S, nb, ax->Ls, ax->comp, ax->E, ax->minb)) {
         ax->path = PATH_FUSED;

@@ -122,7 +122,7 @@ hd_status rows_execute(const hd_plan& pl, const AxisPlan& ax, int64_t count, con
 
 // Plan for an explicit candidate (kernel variant included).
 hd_status plan_create_from(hd_plan** out, const hd_desc* d, const hd_candidate* c);
-bool comp_default();
+bool comp_default(int64_t n);
 // legal, supported candidates of a 1D description (see hd_enumerate_candidates)
 int enumerate_candidates(const hd_desc* d, std::vector<hd_candidate>* out);
 // tuned candidate recorded for the description, if any

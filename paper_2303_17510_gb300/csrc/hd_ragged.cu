@@ -45,7 +45,7 @@ __device__ __noinline__ void fused_tile(const RaggedArgs& ra, const RTile& t, un
     a.ls_pad = t.aux;
     T* st = reinterpret_cast<T*>(smem) + (size_t)g * (A * t.aux + A * FftShape<S, E>::SMEM);
     T* sm = st + A * t.aux;
-    conv1d_body<float, S, E, KIND, MULT, NB, true>(a, 0, valid, tau, st, sm);
+    conv1d_body<float, S, E, KIND, MULT, NB, false>(a, 0, valid, tau, st, sm);
 }
 
 // columns a thread handles together in the column phases (loads in flight)
@@ -82,7 +82,7 @@ __device__ __noinline__ void colbwd_tile(const RaggedArgs& ra, const RTile& t) {
     constexpr int U = col_u(S1) > 4 ? 4 : col_u(S1);
     static_assert(CB % (RT_THREADS * U) == 0, "column tile");
     for (int c = (int)threadIdx.x; c < CB; c += RT_THREADS * U)
-        split_colbwd_multi<float, S1, KIND, true, U>(a, 0, t.count * CB + c, RT_THREADS);
+        split_colbwd_multi<float, S1, KIND, false, U>(a, 0, t.count * CB + c, RT_THREADS);
 }
 
 // configuration id of a FUSED tile
@@ -369,7 +369,7 @@ hd_status ragged_create(hd_plan** out, int64_t n, const hd_desc* descs, const hd
         c.D = 1;
         c.E = c.S <= 4096 ? ragged_E((int)c.S) : kRowE;
         c.minb = 1;
-        c.comp = 1;
+        c.comp = 0;
         rg->cand[i] = c;
         rg->kinds[i] = d->kind;
         RInst& r = rg->inst[i];

@@ -62,11 +62,11 @@ int enumerate_candidates(const hd_desc* d, std::vector<hd_candidate>* out) {
     mpq.emplace_back(next_pow2_t(M), 1, 1);   // explicit zero padding
     Conv1dCfg vars[64];
     const int nv = conv1d_variants(d->dtype, d->kind, vars, 64);
-    const bool comp = d->dtype == HD_F32 && comp_default();
     for (auto& t : mpq) {
         int64_t m = std::get<0>(t), p = std::get<1>(t), q = std::get<2>(t), S, n;
         int nb;
         if (validate_axis(d->kind, d->mult, L, M, m, p, q, &S, &n, &nb) != HD_OK) continue;
+        const bool comp = d->dtype == HD_F32 && comp_default(n);
         const int64_t Ls = d->kind == HD_HERMITIAN ? (L + 1) / 2 : L;
         if (split_supported(d->dtype, d->kind, d->mult, S, nb)) {
             bool dup = false;

@@ -3,7 +3,7 @@
 Tolerances: FP64 on integer-valued inputs must round (rint) to the exact
 oracle result; FP64 on real-valued inputs rel-L2 <= 1e-12; FP32 rel-L2 <=
 1e-5 (the FP32 contract: FFT rounding grows like eps * log2 S, eps = 6e-8,
-and the residue sum is compensated).
+and the residue sum is compensated from 8 residues on).
 """
 import numpy as np
 import pytest
@@ -205,3 +205,24 @@ def test_determinism(hd):
         a = run_conv(hd, plan, fs)
         b = run_conv(hd, plan, fs)
     assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("comp", ["0", "1"])
+@pytest.mark.parametrize("kind", ["complex", "centered", "hermitian"])
+def test_plain_and_compensated_residue_sums(hd, monkeypatch, kind, comp):
+    """Both accumulations of the residue contributions (HD_COMP forces the
+    TwoSum or the plain sum; by default TwoSum is used from 8 residues on)
+    meet the FP32 bound, with few and with many residues."""
+    monkeypatch.setenv("HD_COMP", comp)
+    L = 1000
+    fs = make_inputs(kind, L, 2, 3, 31)
+    ref = direct.conv1d_batch(fs, kind)
+    M = params.dealias_bound(kind, L) + 7
+    for m in (16, 64, 512):
+        try:
+            plan = hd.Plan(L, M, m=m, kind=kind)
+        except hd.HdError as e:
+            assert e.name == "HD_ERR_UNSUPPORTED"
+            continue
+        with plan:
+            check(run_conv(hd, plan, fs), ref, "f32", False, (kind, comp, m, plan.params()))
