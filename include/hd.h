@@ -256,9 +256,11 @@ hd_status hd_selector_choose(const hd_desc* d, hd_candidate* out, int* confident
 /* One ragged plan for n 1D descriptions (ndim = 1 each).  Per instance,
  * m = 0 picks parameters from the tuning cache if it holds the instance's
  * (dtype, kind, mult, L, M), else from the learned selector if one is loaded
- * and confident, else from the cost model.  Allocates the work buffers of the
- * instances whose residue transforms exceed one CTA, the queue of tiles and
- * the graph.  HD_ERR_INVALID on bad descriptions, HD_ERR_ALIASED below a
+ * and confident, else from the cost model.  Allocates the queue of tiles, the
+ * graph and the work buffers of the instances whose residue transforms exceed
+ * one CTA: those instances are packed into groups that take turns in a ring of
+ * four buffers of at most 16 MiB each (larger when one instance needs more),
+ * so the work buffers stay in L2 whatever the batch size.  HD_ERR_INVALID on bad descriptions, HD_ERR_ALIASED below a
  * dealiasing bound, HD_ERR_UNSUPPORTED when no parameters fit. */
 hd_status hd_ragged_create(hd_plan** out, int64_t n, const hd_desc* descs);
 

@@ -213,8 +213,8 @@ hd_status plan_create_nd(hd_plan** out, const hd_desc* d) {
     if (st == HD_OK && pl->ax[nd - 1].path == PATH_SPLIT) {
         AxisPlan& ax = pl->ax[nd - 1];
         const size_t per = (size_t)d->A * (size_t)ax.n * (size_t)ax.S * esz;
-        int64_t ch = (int64_t)((128u << 20) / per);
-        ax.chunk = ch < 1 ? 1 : (ch > 64 ? 64 : ch);
+        int64_t ch = (int64_t)((64u << 20) / per);   // as 1D plans: at most 64 MiB, L2-resident
+        ax.chunk = ch < 1 ? 1 : (ch > 2048 ? 2048 : ch);
         if (cudaMalloc(&pl->scratch, per * (size_t)ax.chunk) != cudaSuccess) {
             cudaGetLastError();
             pl->scratch = nullptr;

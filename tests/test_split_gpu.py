@@ -62,6 +62,8 @@ def test_split_chunking_and_inplace(hd):
     ref = cdirect.conv1d_batch([f[ref_idx] for f in fs], L, "complex")
     c = split_cands(hd, L=L, M=M)[0]
     with hd.Plan(L, M, candidate=c) as plan:
+        per_instance = 2 * c["n"] * c["S"] * 8          # work buffer: A n S complex64 values
+        assert plan.params()["scratch_bytes"] // per_instance < count   # several chunks
         d = [torch.from_numpy(f.astype(np.complex64)).cuda() for f in fs]
         plan.convolve_batched(d, d[0], count, L)
         torch.cuda.synchronize()
