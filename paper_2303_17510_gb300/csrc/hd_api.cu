@@ -20,6 +20,13 @@ using namespace hd;
 namespace hd {
 
 int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+int64_t next_pow2_t(int64_t x) {
+    int64_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
 bool is_pow2(int64_t x) { return x > 0 && (x & (x - 1)) == 0; }
 
 // zeta_N^k = exp(2 pi i k / N) in FP64.  The angle is reduced exactly to the

@@ -50,6 +50,16 @@ void derive_pq(int kind, int64_t L, int64_t M, int64_t m, int64_t* p, int64_t* q
     int64_t pp = *p, qq = *q, nn;
     if (pp == 0) {
         hd_derive_params(kind, L, M, m, &pp, &qq, &nn);
+        // the transform size S = p m (complex) or p m / 2 (centered, Hermitian)
+        // must be a power of two: round p up (explicit padding to a longer
+        // p m, which hybrid padding allows) when the paper's p gives another S
+        if (kind == HD_COMPLEX && pp > 2 && !is_pow2(pp)) {
+            pp = next_pow2_t(pp);
+            qq = ceil_div(M, pp * m) * pp;
+        } else if (kind != HD_COMPLEX && pp > 2 && !is_pow2(pp / 2)) {
+            pp = 2 * next_pow2_t(pp / 2);
+            qq = ceil_div(2 * M, pp * m) * (pp / 2);
+        }
         if (*q != 0) qq = *q;
     } else if (qq == 0) {
         if (pp == 1 && m >= M) {

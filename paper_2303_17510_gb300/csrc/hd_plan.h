@@ -39,6 +39,7 @@ struct AxisPlan {
 };
 
 int64_t ceil_div(int64_t a, int64_t b);
+int64_t next_pow2_t(int64_t x);   // smallest power of two >= x
 bool is_pow2(int64_t x);
 void zeta_fp64(int64_t k, int64_t N, double* c, double* s);
 hd_status upload_zetas(const std::vector<std::pair<int64_t, int64_t>>& ek, int dtype, void** dev);

@@ -16,12 +16,6 @@ namespace hd {
 
 namespace {
 
-int64_t next_pow2_t(int64_t x) {
-    int64_t p = 1;
-    while (p < x) p <<= 1;
-    return p;
-}
-
 bool desc_ok_1d(const hd_desc* d) {
     if (!d || d->ndim != 1) return false;
     if (d->kind < HD_COMPLEX || d->kind > HD_HERMITIAN) return false;
