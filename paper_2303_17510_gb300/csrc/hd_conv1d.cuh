@@ -71,25 +71,34 @@ __device__ __forceinline__ void acc_add(R& s, R& c, R x) {
     }
 }
 
+// Input element i: a plain load, or (STREAM) a streaming global load marked
+// evict-first, for inputs read once from HBM that should not displace
+// L2-resident work buffers.
+template <bool STREAM, class T>
+__device__ __forceinline__ T ld_in(const T* f, int i) {
+    if constexpr (STREAM) return __ldcs(f + i);
+    else return f[i];
+}
+
 // Stored input value(s) folded to transform slot j (see header comment).
 // Returns block-0 and block-1 values (block 1 is conj-mirrored for Hermitian).
-template <int KIND, class T>
+template <int KIND, bool STREAM = false, class T>
 __device__ __forceinline__ void load_fold(const T* f, int j, int S, const ConvArgs& a, bool valid, T& b0, T& b1) {
     b0 = czero<T>();
     b1 = czero<T>();
     if (!valid) return;
     if constexpr (KIND == KIND_COMPLEX) {
-        if (j < a.L) b0 = f[j];
-        if (j + S < a.L) b1 = f[j + S];
+        if (j < a.L) b0 = ld_in<STREAM>(f, j);
+        if (j + S < a.L) b1 = ld_in<STREAM>(f, j + S);
     } else if constexpr (KIND == KIND_CENTERED) {
-        if (j < a.L - a.H) b0 = f[j + a.H];
-        if (j >= S - a.H) b1 = f[j - S + a.H];
+        if (j < a.L - a.H) b0 = ld_in<STREAM>(f, j + a.H);
+        if (j >= S - a.H) b1 = ld_in<STREAM>(f, j - S + a.H);
     } else {
         if (j < a.Ls) {
-            b0 = f[j];
+            b0 = ld_in<STREAM>(f, j);
             if (j == 0) b0.y = 0;
         }
-        if (j > 0 && S - j < a.Ls) b1 = cconj(f[S - j]);
+        if (j > 0 && S - j < a.Ls) b1 = cconj(ld_in<STREAM>(f, S - j));
     }
 }
 

@@ -293,7 +293,8 @@ __device__ __forceinline__ void fft_pass(T* v, const TW& tw, int tau) {
 }
 
 // Exchange between pass k and pass k+1 for NA arrays (array a uses the padded
-// buffer sm + a * SMEM).  FWD: from the layout after pass k to the layout pass
+// buffer sm + a * SMEM).  Padded slots of x + D with D a multiple of 16 are
+// padidx(x) + D + D/16, so each group of accesses computes one padded base.  FWD: from the layout after pass k to the layout pass
 // k+1 reads; otherwise the reverse.  Two barriers: after the writes, and
 // before the buffers are written again.  CST > 1 interleaves the buffers of
 // CST independent transforms (one per column of a column tile): slot s of the
@@ -309,21 +310,27 @@ __device__ __forceinline__ void fft_exchange(T* v, T* sm, int tau) {
 #pragma unroll
         for (int beta = 0; beta < E / R; ++beta) {
             const int nu = tau + Sh::T * beta;
+            const int pn = padidx(nu);
 #pragma unroll
-            for (int k1 = 0; k1 < R; ++k1)
+            for (int k1 = 0; k1 < R; ++k1) {
+                const int idx = (V % 16 == 0) ? pn + V * k1 + (V / 16) * k1 : padidx(nu + V * k1);
 #pragma unroll
-                for (int a = 0; a < NA; ++a) sm[(a * Sh::SMEM + padidx(nu + V * k1)) * CST] = v[a * E + beta * R + k1];
+                for (int a = 0; a < NA; ++a) sm[(a * Sh::SMEM + idx) * CST] = v[a * E + beta * R + k1];
+            }
         }
         __syncthreads();
 #pragma unroll
         for (int beta = 0; beta < E / Rn; ++beta) {
             const int nu = tau + Sh::T * beta;
             const int b = nu / Qn, c = nu & (Qn - 1);
+            const int base = b * Rn * Qn + c;
+            const int pb = padidx(base);
 #pragma unroll
-            for (int i = 0; i < Rn; ++i)
+            for (int i = 0; i < Rn; ++i) {
+                const int idx = (Qn % 16 == 0) ? pb + i * Qn + (Qn / 16) * i : padidx(base + i * Qn);
 #pragma unroll
-                for (int a = 0; a < NA; ++a)
-                    v[a * E + beta * Rn + i] = sm[(a * Sh::SMEM + padidx(b * Rn * Qn + i * Qn + c)) * CST];
+                for (int a = 0; a < NA; ++a) v[a * E + beta * Rn + i] = sm[(a * Sh::SMEM + idx) * CST];
+            }
         }
         __syncthreads();
     } else {
@@ -331,20 +338,26 @@ __device__ __forceinline__ void fft_exchange(T* v, T* sm, int tau) {
         for (int beta = 0; beta < E / Rn; ++beta) {
             const int nu = tau + Sh::T * beta;
             const int b = nu / Qn, c = nu & (Qn - 1);
+            const int base = b * Rn * Qn + c;
+            const int pb = padidx(base);
 #pragma unroll
-            for (int i = 0; i < Rn; ++i)
+            for (int i = 0; i < Rn; ++i) {
+                const int idx = (Qn % 16 == 0) ? pb + i * Qn + (Qn / 16) * i : padidx(base + i * Qn);
 #pragma unroll
-                for (int a = 0; a < NA; ++a)
-                    sm[(a * Sh::SMEM + padidx(b * Rn * Qn + i * Qn + c)) * CST] = v[a * E + beta * Rn + i];
+                for (int a = 0; a < NA; ++a) sm[(a * Sh::SMEM + idx) * CST] = v[a * E + beta * Rn + i];
+            }
         }
         __syncthreads();
 #pragma unroll
         for (int beta = 0; beta < E / R; ++beta) {
             const int nu = tau + Sh::T * beta;
+            const int pn = padidx(nu);
 #pragma unroll
-            for (int k1 = 0; k1 < R; ++k1)
+            for (int k1 = 0; k1 < R; ++k1) {
+                const int idx = (V % 16 == 0) ? pn + V * k1 + (V / 16) * k1 : padidx(nu + V * k1);
 #pragma unroll
-                for (int a = 0; a < NA; ++a) v[a * E + beta * R + k1] = sm[(a * Sh::SMEM + padidx(nu + V * k1)) * CST];
+                for (int a = 0; a < NA; ++a) v[a * E + beta * R + k1] = sm[(a * Sh::SMEM + idx) * CST];
+            }
         }
         __syncthreads();
     }

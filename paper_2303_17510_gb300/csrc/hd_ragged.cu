@@ -70,7 +70,7 @@ template <int KIND, int MULT>
 __device__ __noinline__ void row_tile(const RaggedArgs& ra, const RTile& t, unsigned char* smem) {
     const RInst& r = ra.inst[t.first];
     const SplitArgs a = split_args_of(r);
-    split_row_body<float, kRowS2, kRowE, KIND, MULT>(a, t.count, true, (int)threadIdx.x,
+    split_row_body<float, kRowS2, kRowE, KIND, MULT, true>(a, t.count, true, (int)threadIdx.x,
                                                      reinterpret_cast<float2*>(smem));
 }
 
@@ -83,6 +83,12 @@ __device__ __noinline__ void colbwd_tile(const RaggedArgs& ra, const RTile& t) {
     static_assert(CB % (RT_THREADS * U) == 0, "column tile");
     for (int c = (int)threadIdx.x; c < CB; c += RT_THREADS * U)
         split_colbwd_multi<float, S1, KIND, false, U>(a, 0, t.count * CB + c, RT_THREADS);
+    // the tile's columns of the work buffer are dead: drop them from L2
+    __syncthreads();
+    const float2* base = static_cast<const float2*>(a.work);
+    for (int rk = 0; rk < a.n * S1; ++rk)
+        l2_discard(base + (int64_t)(rk / S1) * a.S + (int64_t)(rk % S1) * a.S2 + (int64_t)t.count * CB,
+                   (int64_t)CB * sizeof(float2), (int)threadIdx.x, RT_THREADS);
 }
 
 // configuration id of a FUSED tile

@@ -7,7 +7,8 @@
 //     X_{k1 + S1 k2} = sum_{j2} zeta_{S2}^{j2 k2} zeta_S^{j2 k1}
 //                      sum_{j1} zeta_{S1}^{j1 k1} W_{j1 S2 + j2}.
 // Three kernels per batch chunk, with the work buffer of Section 5 (A n S
-// values per instance) in device scratch:
+// values per instance) in device scratch; inputs are read and outputs written
+// with evict-first hints so that the work buffer stays in L2 between phases:
 //   split_colfwd : per (instance, input a, residue r, column j2): fold and twist
 //                  the stored input into W_{j1 S2 + j2}, DFT over j1, twiddle,
 //                  store row k1 of the work buffer;
@@ -46,6 +47,16 @@ __device__ __forceinline__ void dft_small(T* v) {
     dft_reg<S1, INV>(v);
 }
 
+// Drops the L2 lines of a work-buffer region whose values are dead, without
+// writing them back to DRAM (the region's contents become undefined until it
+// is written again).  The region starts on a 128-byte boundary and spans a
+// multiple of 128 bytes; threads tid = 0 .. nthreads-1 share the lines.
+__device__ __forceinline__ void l2_discard(const void* p, int64_t bytes, int tid, int nthreads) {
+    const char* c = static_cast<const char*>(p);
+    for (int64_t off = (int64_t)tid * 128; off < bytes; off += (int64_t)nthreads * 128)
+        asm volatile("discard.global.L2 [%0], 128;" ::"l"(c + off) : "memory");
+}
+
 // Forward column j2 of residue r of input aa of instance inst.
 template <class R, int S1, int KIND>
 __device__ __forceinline__ void split_colfwd_body(const SplitArgs& a, int64_t inst, int aa, int r, int j2) {
@@ -64,7 +75,7 @@ __device__ __forceinline__ void split_colfwd_body(const SplitArgs& a, int64_t in
     for (int j1 = 0; j1 < S1; ++j1) {
         const int j = j1 * a.S2 + j2;
         T b0, b1;
-        load_fold<KIND>(f, j, a.S, ca, true, b0, b1);
+        load_fold<KIND, true>(f, j, a.S, ca, true, b0, b1);
         v[j1] = cmul(cadd(b0, cmul(cr, b1)), ldtw(twR + (int64_t)r * a.S + j));
     }
     dft_small<S1, false>(v);
@@ -100,7 +111,7 @@ __device__ __forceinline__ void split_colfwd_multi(const SplitArgs& a, int64_t i
         for (int j1 = 0; j1 < S1; ++j1) {
             const int j = j1 * a.S2 + j2base + u * jstep;
             T b0, b1;
-            load_fold<KIND>(f, j, a.S, ca, true, b0, b1);
+            load_fold<KIND, true>(f, j, a.S, ca, true, b0, b1);
             v[u][j1] = cmul(cadd(b0, cmul(cr, b1)), ldtw(twR + (int64_t)r * a.S + j));
         }
     }
@@ -133,7 +144,10 @@ __global__ void __launch_bounds__(256) split_colfwd(const __grid_constant__ Spli
 
 // Row `row` (= (instance * n + r) * S1 + k1) for one group of S2/E threads;
 // sm is the group's A exchange buffers.
-template <class R, int S2, int E, int KIND, int MULT>
+// DISCARD: drop the dead input rows a >= 1 from L2 once they are loaded (the
+// persistent ragged kernel, whose work buffers would otherwise be written back
+// to DRAM; measured slower than leaving them for the batched kernels).
+template <class R, int S2, int E, int KIND, int MULT, bool DISCARD = false>
 __device__ __forceinline__ void split_row_body(const SplitArgs& a, int64_t row, bool valid, int tau, cplx<R>* sm) {
     using T = cplx<R>;
     using Sh = FftShape<S2, E>;
@@ -153,6 +167,14 @@ __device__ __forceinline__ void split_row_body(const SplitArgs& a, int64_t row, 
         for (int e = 0; e < E; ++e) v[aa * E + e] = valid ? src[tau + TT * e] : czero<T>();
     }
     fft_forward<S2, E, A>(v, sm, tw, tau);
+    // rows a >= 1 are dead once every thread has loaded them (the forward
+    // transform's exchanges put barriers in between); row 0 receives the result
+    if (DISCARD && valid) {
+#pragma unroll
+        for (int aa = 1; aa < A; ++aa)
+            l2_discard(base + ((inst * A + aa) * a.n + r) * (int64_t)a.S + (int64_t)k1 * S2, (int64_t)S2 * sizeof(T),
+                       tau, TT);
+    }
     T p[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
@@ -252,13 +274,13 @@ __device__ __forceinline__ void split_colbwd_body(const SplitArgs& a, int64_t in
             o1 = mk<T>(x1 * sc, y1 * sc);
         }
         if constexpr (KIND == KIND_COMPLEX) {
-            if (j < a.L) hout[j] = o0;
-            if (j + a.S < a.L) hout[j + a.S] = o1;
+            if (j < a.L) __stcs(hout + j, o0);
+            if (j + a.S < a.L) __stcs(hout + j + a.S, o1);
         } else if constexpr (KIND == KIND_CENTERED) {
-            if (j < a.L - a.H) hout[j + a.H] = o0;
-            if (j >= a.S - a.H) hout[j - a.S + a.H] = o1;
+            if (j < a.L - a.H) __stcs(hout + j + a.H, o0);
+            if (j >= a.S - a.H) __stcs(hout + j - a.S + a.H, o1);
         } else {
-            if (j < a.Ls) hout[j] = o0;
+            if (j < a.Ls) __stcs(hout + j, o0);
         }
     }
 }
@@ -333,13 +355,13 @@ __device__ __forceinline__ void split_colbwd_multi(const SplitArgs& a, int64_t i
                 o1 = mk<T>(x1 * sc, y1 * sc);
             }
             if constexpr (KIND == KIND_COMPLEX) {
-                if (j < a.L) hout[j] = o0;
-                if (j + a.S < a.L) hout[j + a.S] = o1;
+                if (j < a.L) __stcs(hout + j, o0);
+                if (j + a.S < a.L) __stcs(hout + j + a.S, o1);
             } else if constexpr (KIND == KIND_CENTERED) {
-                if (j < a.L - a.H) hout[j + a.H] = o0;
-                if (j >= a.S - a.H) hout[j - a.S + a.H] = o1;
+                if (j < a.L - a.H) __stcs(hout + j + a.H, o0);
+                if (j >= a.S - a.H) __stcs(hout + j - a.S + a.H, o1);
             } else {
-                if (j < a.Ls) hout[j] = o0;
+                if (j < a.Ls) __stcs(hout + j, o0);
             }
         }
     }
