@@ -734,7 +734,20 @@ def run_ragged(args, ctx, hd):
         setup["selector"] = time.perf_counter() - t0
         res["selector"] = timed(p, "timed")
         sel = [p.params(i) for i in range(len(descs))]
-    clocks = clk.stop()
+        clocks = clk.stop()
+        # end to end through the C ABI: pinned host inputs -> device buffers the plan is bound to
+        # -> one ragged launch -> pinned host outputs
+        h_in = [x.cpu().pin_memory() for x in base]
+        h_out = torch.empty(tot, dtype=torch.complex64).pin_memory()
+
+        def e2e_step():
+            for a in range(3):
+                base[a].copy_(h_in[a], non_blocking=True)
+            p.run(ctx.stream)
+            h_out.copy_(outb, non_blocking=True)
+        e2e_ms = ctx.max_over_ranks(ctx.time_it(e2e_step, max(3, min(args.steps, 10))))
+        e2e = {"value": ctx.job_rate(len(descs), e2e_ms), "unit": "conv/s", "h2d_bytes_per_step": 3 * tot * 8,
+               "d2h_bytes_per_step": tot * 8, "ms_per_step": e2e_ms}
     hd.selector_clear()
     out_sel = outb.clone()
     matched = None
@@ -777,7 +790,7 @@ def run_ragged(args, ctx, hd):
                 "selector_vs_cost_model": res["selector"] / res["cost_model"],
                 "roofline": roofline(bytes_, ms, read_traffic("ragged"), "ragged_kernel"),
                 "accuracy": {"rel_l2_sampled_max": max(errs), "instances": len(pick)},
-                "gpu_launches": reps, "clocks": clocks})
+                "e2e": e2e, "gpu_launches": reps, "clocks": clocks})
     if ctx.rank == 0 and not args.no_cpu_baseline:
         rate, nt, sample = oracle_rate_ragged(10.0, descs)
         out["cpu_baseline"] = {"value": rate, "unit": "conv/s", "cores": nt, "kind": "oracle", "sample": sample}
