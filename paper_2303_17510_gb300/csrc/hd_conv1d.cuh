@@ -54,6 +54,7 @@ struct ConvArgs {
     const void* twS;    // FFT pass twiddles (FftShape<S, E> layout)
     const void* twN;    // residue twists: zeta_N^{r j} at r S + j (r < n, j < S), then zeta_N^{r S} at n S + r
     double invN;        // 1 / N
+    int* err;           // persistent kernel: set to 1 when a bounded wait runs out (may be null)
 };
 
 // Residue-sum accumulation.  COMP: TwoSum compensated s + c += x (FP32 path);
@@ -115,7 +116,8 @@ struct ConvLaunch {
 // same sequence of barriers (groups of one CTA share n).  FFT twiddles are
 // read through the read-only data cache (a shared-memory table measured
 // slower: it competes with the exchanges for shared-memory bandwidth).
-template <class R, int S, int E, int KIND, int MULT, int NB, bool COMP>
+// STAGE = false: the inputs are already in st (staged by bulk copies).
+template <class R, int S, int E, int KIND, int MULT, int NB, bool COMP, bool STAGE = true>
 __device__ __forceinline__ void conv1d_body(const ConvArgs& a, int64_t inst, bool valid, int tau, cplx<R>* st,
                                             cplx<R>* sm) {
     using T = cplx<R>;
@@ -125,16 +127,18 @@ __device__ __forceinline__ void conv1d_body(const ConvArgs& a, int64_t inst, boo
     const T* twN = static_cast<const T*>(a.twN);
     const TwGlobal<T> twS{static_cast<const T*>(a.twS)};
 
-    // stage the A inputs of this convolution in shared memory (coalesced)
-    if (valid) {
+    if constexpr (STAGE) {
+        // stage the A inputs of this convolution in shared memory (coalesced)
+        if (valid) {
 #pragma unroll
-        for (int aa = 0; aa < A; ++aa) {
-            const T* src = static_cast<const T*>(a.f[aa]) + inst * a.stride;
-            T* dst = st + aa * a.ls_pad;
-            for (int i = tau; i < a.Ls; i += TT) dst[i] = __ldcs(src + i);   // streamed: keep L1 for the tables
+            for (int aa = 0; aa < A; ++aa) {
+                const T* src = static_cast<const T*>(a.f[aa]) + inst * a.stride;
+                T* dst = st + aa * a.ls_pad;
+                for (int i = tau; i < a.Ls; i += TT) dst[i] = __ldcs(src + i);   // streamed: keep L1 for the tables
+            }
         }
+        __syncthreads();
     }
-    __syncthreads();
 
     R s0[2 * E], c0[COMP ? 2 * E : 1];
     R s1[NB == 2 ? 2 * E : 1], c1[(NB == 2 && COMP) ? 2 * E : 1];
@@ -309,6 +313,127 @@ __global__ void __launch_bounds__(ConvLaunch<S, E>::MAXT, MINB) conv1d_kernel(co
     T* sm = st + A * a.ls_pad;
     const int64_t inst = (int64_t)blockIdx.x * G + g;
     conv1d_body<R, S, E, KIND, MULT, NB, COMP>(a, inst, inst < a.count, tau, st, sm);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent variant with double-buffered staging by bulk copies.
+//
+// One CTA per SM loops over its share of the batch.  Thread 0 stages the
+// inputs of the next convolution(s) into the second staging buffer with
+// cp.async.bulk (the TMA engine copies global -> shared, completion counted
+// on an mbarrier) while the CTA computes on the first, so the HBM latency of
+// the next batch element is hidden behind the current one's transforms.
+// Rows must start on 16-byte boundaries and span a multiple of 16 bytes
+// (checked by the launcher).  Every wait on an mbarrier is bounded in time:
+// a wait that runs out sets *err to 1 and the CTA returns after a bounded
+// wait for its other copy in flight.
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+// thread 0: expect `bytes` of transactions on bar and arrive
+__device__ __forceinline__ void mbar_expect(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ long long conv_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return (long long)t;
+}
+
+// bounded wait for the phase with the given parity (about 2 s)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const long long t0 = conv_ns();
+    while (!mbar_try(bar, parity))
+        if (conv_ns() - t0 > 2000000000LL) return false;
+    return true;
+}
+
+template <class R, int S, int E, int KIND, int MULT, int NB, bool COMP>
+__global__ void __launch_bounds__(ConvLaunch<S, E>::MAXT, 1) conv1d_kernel_pipe(const __grid_constant__ ConvArgs a) {
+    using T = cplx<R>;
+    using Sh = FftShape<S, E>;
+    constexpr int TT = Sh::T;
+    constexpr int A = (MULT == MULT_PRODUCT) ? 2 : 3;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ int s_ok;
+    const int G = blockDim.x / TT;
+    const int g = threadIdx.x / TT;
+    const int tau = threadIdx.x - g * TT;
+    const size_t stage_elems = (size_t)G * A * a.ls_pad;          // one staging buffer (all groups)
+    T* stage0 = reinterpret_cast<T*>(smem_raw);
+    T* sm = stage0 + 2 * stage_elems + (size_t)g * A * Sh::SMEM;
+    const int64_t nsteps = (a.count + G - 1) / G;                    // CTA steps over the batch
+    const uint32_t row_bytes = (uint32_t)(a.Ls * sizeof(T));
+
+    // thread 0: stage step `k` (G convolutions) into buffer b
+    auto issue = [&](int64_t k, int b) {
+        uint32_t bytes = 0;
+        for (int gg = 0; gg < G; ++gg)
+            if (k * G + gg < a.count) bytes += A * row_bytes;
+        mbar_expect(&bar[b], bytes);
+        for (int gg = 0; gg < G; ++gg) {
+            const int64_t inst = k * G + gg;
+            if (inst >= a.count) break;
+#pragma unroll
+            for (int aa = 0; aa < A; ++aa)
+                bulk_g2s(stage0 + b * stage_elems + ((size_t)gg * A + aa) * a.ls_pad,
+                         static_cast<const T*>(a.f[aa]) + inst * a.stride, row_bytes, &bar[b]);
+        }
+    };
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    int64_t k = blockIdx.x;
+    if (k >= nsteps) return;
+    if (threadIdx.x == 0) issue(k, 0);
+    for (int it = 0; k < nsteps; ++it, k += gridDim.x) {
+        const int b = it & 1;
+        const int64_t kn = k + gridDim.x;
+        if (threadIdx.x == 0 && kn < nsteps) issue(kn, b ^ 1);   // buffer b^1 was released by the last barrier
+        if (threadIdx.x == 0) s_ok = mbar_wait(&bar[b], (uint32_t)((it >> 1) & 1)) ? 1 : 0;
+        __syncthreads();
+        if (!s_ok) {
+            if (threadIdx.x == 0) {
+                if (a.err) atomicExch(a.err, 1);
+                if (kn < nsteps) mbar_wait(&bar[b ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
+            }
+            return;
+        }
+        mbar_try(&bar[b], (uint32_t)((it >> 1) & 1));                // this thread's own acquire of the phase
+        const int64_t inst = k * G + g;
+        conv1d_body<R, S, E, KIND, MULT, NB, COMP, false>(a, inst, inst < a.count, tau,
+                                                          stage0 + b * stage_elems + (size_t)g * A * a.ls_pad, sm);
+        __syncthreads();
+    }
 }
 
 // Forward transform of one residue of one input, written in the paper's

@@ -1,6 +1,10 @@
 // hd_conv1d_tu.cuh -- instantiation table of the fused 1D kernels for one
 // (dtype, kind) pair.  Included by the hd_conv1d_<dtype>_<kind>.cu files with
 // HD_REAL, HD_KIND, HD_DT, HD_KN and HD_SE_EXTRA defined.
+#include <algorithm>
+#include <cstdint>
+#include <cstdlib>
+
 #include "hd_dispatch.h"
 
 namespace hd {
@@ -23,9 +27,82 @@ int groups_for(int ls_pad) {
     return per > kMaxSmemPerBlock ? 0 : G;
 }
 
+// error word of the persistent kernels of this unit (a bounded wait ran out)
+__device__ int g_pipe_err;
+
+int* pipe_err_ptr() {
+    static int* ptrs[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    if (!ptrs[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_pipe_err) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        ptrs[dev] = static_cast<int*>(p);
+    }
+    return ptrs[dev];
+}
+
+// Persistent CTAs with bulk-copy staging (conv1d_kernel_pipe): for the
+// one-CTA-per-SM variants, when both staging buffers fit and every row is a
+// whole number of 16-byte units on a 16-byte boundary.  HD_PIPE=0 turns it off.
+template <class R, int S, int E, int KIND, int MULT, int NB, bool COMP>
+cudaError_t launch_pipe(const ConvArgs& a0, cudaStream_t st, bool* used) {
+    constexpr int T = S / E;
+    constexpr int A = MULT == MULT_PRODUCT ? 2 : 3;
+    *used = false;
+    static const bool enabled = [] {
+        const char* e = std::getenv("HD_PIPE");
+        return !(e && e[0] == '0');
+    }();
+    if (!enabled) return cudaSuccess;
+    const size_t esz = sizeof(cplx<R>);
+    for (int aa = 0; aa < A; ++aa)
+        if (reinterpret_cast<uintptr_t>(a0.f[aa]) % 16 != 0) return cudaSuccess;
+    if ((a0.stride * esz) % 16 != 0 || (a0.Ls * esz) % 16 != 0 || (a0.ls_pad * esz) % 16 != 0) return cudaSuccess;
+    int G = 256 / T;
+    if (G < 1) G = 1;
+    const size_t fft = size_t(A) * FftShape<S, E>::SMEM * esz;
+    const size_t stg = size_t(A) * a0.ls_pad * esz;
+    while (G > 1 && G * (2 * stg + fft) > kMaxSmemPerBlock - 64) --G;
+    const size_t smem = size_t(G) * (2 * stg + fft);
+    if (smem > kMaxSmemPerBlock - 64) return cudaSuccess;
+    auto k = conv1d_kernel_pipe<R, S, E, KIND, MULT, NB, COMP>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cudaSuccess;
+    }
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, G * T, smem) != cudaSuccess || per < 1) {
+        cudaGetLastError();
+        return cudaSuccess;
+    }
+    ConvArgs a = a0;
+    a.err = pipe_err_ptr();
+    const int64_t steps = (a.count + G - 1) / G;
+    if (steps <= 0) {
+        *used = true;
+        return cudaSuccess;
+    }
+    const int64_t grid = std::min<int64_t>(steps, (int64_t)sms * per);
+    k<<<dim3((unsigned)grid), dim3(G * T), smem, st>>>(a);
+    *used = true;
+    return cudaGetLastError();
+}
+
 template <class R, int S, int E, int KIND, int MULT, int NB, bool COMP, int MINB>
 cudaError_t launch_one(const ConvArgs& a, cudaStream_t st) {
     constexpr int T = S / E;
+    if constexpr (MINB == 1) {
+        bool used = false;
+        cudaError_t e = launch_pipe<R, S, E, KIND, MULT, NB, COMP>(a, st, &used);
+        if (used || e != cudaSuccess) return e;
+    }
     const int G = groups_for<R, S, E, MULT>(a.ls_pad);
     if (G < 1) return cudaErrorInvalidValue;
     const size_t smem = size_t(G) * group_smem<R, S, E, MULT>(a.ls_pad);
