@@ -57,6 +57,11 @@ struct ConvArgs {
     int* err;           // persistent kernel: set to 1 when a bounded wait runs out (may be null)
 };
 
+template <bool B>
+struct BoolTag {
+    static constexpr bool value = B;
+};
+
 // Residue-sum accumulation.  COMP: TwoSum compensated s + c += x (FP32 path);
 // otherwise a plain sum.
 template <class R, bool COMP>
@@ -159,25 +164,28 @@ __device__ __forceinline__ void conv1d_body(const ConvArgs& a, int64_t inst, boo
     R dummy = R(0);
 
     if constexpr (KIND != KIND_HERMITIAN) {
-        for (int r = 0; r < a.n; ++r) {
+        // residue r; R0: r = 0, whose twists are all 1 (no loads, no multiplies)
+        auto residue = [&](int r, auto r0_tag) {
+            constexpr bool R0 = decltype(r0_tag)::value;
             const T* twr = twN + (int64_t)r * S;        // zeta_N^{r j}, j < S
-            T cr = ldtw(twN + (int64_t)a.n * S + r);    // zeta_N^{r S}
+            T cr = R0 ? mk<T>(1, 0) : ldtw(twN + (int64_t)a.n * S + r);    // zeta_N^{r S}
             if constexpr (KIND == KIND_CENTERED) cr = cconj(cr);
             T v[A * E];
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const int j = tau + TT * e;
-                const T tw = ldtw(twr + j);
+                const T tw = R0 ? mk<T>(1, 0) : ldtw(twr + j);
 #pragma unroll
                 for (int aa = 0; aa < A; ++aa) {
                     if constexpr (KIND == KIND_COMPLEX && NB == 1) {
                         // L <= S: one block, nothing folds in
                         const T* sa = st + aa * a.ls_pad;
-                        v[aa * E + e] = (valid && j < a.L) ? cmul(sa[j], tw) : czero<T>();
+                        const T x = (valid && j < a.L) ? sa[j] : czero<T>();
+                        v[aa * E + e] = R0 ? x : cmul(x, tw);
                     } else {
                         T b0, b1;
                         load_fold<KIND>(st + aa * a.ls_pad, j, S, a, valid, b0, b1);
-                        v[aa * E + e] = cmul(cadd(b0, cmul(cr, b1)), tw);
+                        v[aa * E + e] = R0 ? cadd(b0, b1) : cmul(cadd(b0, cmul(cr, b1)), tw);
                     }
                 }
             }
@@ -195,16 +203,18 @@ __device__ __forceinline__ void conv1d_body(const ConvArgs& a, int64_t inst, boo
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const int j = tau + TT * e;
-                const T y = cmulc(p[e], ldtw(twr + j));        // zeta_N^{-r j} y_j
+                const T y = R0 ? p[e] : cmulc(p[e], ldtw(twr + j));        // zeta_N^{-r j} y_j
                 acc_add<R, COMP>(s0[2 * e], COMP ? c0[2 * e] : dummy, y.x);
                 acc_add<R, COMP>(s0[2 * e + 1], COMP ? c0[2 * e + 1] : dummy, y.y);
                 if constexpr (NB == 2) {
-                    const T y1 = cmulc(y, cr);                 // block 1: extra zeta_N^{-r o}
+                    const T y1 = R0 ? y : cmulc(y, cr);                 // block 1: extra zeta_N^{-r o}
                     acc_add<R, COMP>(s1[2 * e], COMP ? c1[2 * e] : dummy, y1.x);
                     acc_add<R, COMP>(s1[2 * e + 1], COMP ? c1[2 * e + 1] : dummy, y1.y);
                 }
             }
-        }
+        };
+        residue(0, BoolTag<true>{});
+        for (int r = 1; r < a.n; ++r) residue(r, BoolTag<false>{});
     } else {
         for (int r1 = 0; r1 < a.n; r1 += 2) {
             const int r2 = r1 + 1;
