@@ -216,24 +216,26 @@ __device__ __forceinline__ void conv1d_body(const ConvArgs& a, int64_t inst, boo
         residue(0, BoolTag<true>{});
         for (int r = 1; r < a.n; ++r) residue(r, BoolTag<false>{});
     } else {
-        for (int r1 = 0; r1 < a.n; r1 += 2) {
+        // residue pair (r1, r1 + 1); R0: r1 = 0, whose twists are all 1
+        auto pair = [&](int r1, auto r0_tag) {
+            constexpr bool R0 = decltype(r0_tag)::value;
             const int r2 = r1 + 1;
             const bool has2 = r2 < a.n;
             const T* twr1 = twN + (int64_t)r1 * S;
             const T* twr2 = twN + (int64_t)(has2 ? r2 : r1) * S;
-            const T cr1 = cconj(ldtw(twN + (int64_t)a.n * S + r1));      // zeta_N^{-r1 S}
+            const T cr1 = R0 ? mk<T>(1, 0) : cconj(ldtw(twN + (int64_t)a.n * S + r1));      // zeta_N^{-r1 S}
             const T cr2 = has2 ? cconj(ldtw(twN + (int64_t)a.n * S + r2)) : czero<T>();
             T v[A * E];
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const int j = tau + TT * e;
-                const T t1 = ldtw(twr1 + j);
+                const T t1 = R0 ? mk<T>(1, 0) : ldtw(twr1 + j);
                 const T t2 = has2 ? ldtw(twr2 + j) : czero<T>();
 #pragma unroll
                 for (int aa = 0; aa < A; ++aa) {
                     T b0, b1;
                     load_fold<KIND>(st + aa * a.ls_pad, j, S, a, valid, b0, b1);
-                    const T w1 = cmul(cadd(b0, cmul(cr1, b1)), t1);
+                    const T w1 = R0 ? cadd(b0, b1) : cmul(cadd(b0, cmul(cr1, b1)), t1);
                     const T w2 = cmul(cadd(b0, cmul(cr2, b1)), t2);
                     v[aa * E + e] = mk<T>(w1.x - w2.y, w1.y + w2.x);   // W1 + i W2
                 }
@@ -265,13 +267,15 @@ __device__ __forceinline__ void conv1d_body(const ConvArgs& a, int64_t inst, boo
                 const T g1 = mk<T>((yj.x + ym.x) * hf, (yj.y - ym.y) * hf);   // (Y_j + conj Y_{S-j}) / 2
                 const T d = mk<T>(yj.x - ym.x, yj.y + ym.y);                  // Y_j - conj Y_{S-j}
                 const T g2 = mk<T>(d.y * hf, -d.x * hf);                       // d / (2i)
-                T y = cmulc(g1, ldtw(twr1 + j));
+                T y = R0 ? g1 : cmulc(g1, ldtw(twr1 + j));
                 if (has2) y = cadd(y, cmulc(g2, ldtw(twr2 + j)));
                 acc_add<R, COMP>(s0[2 * e], COMP ? c0[2 * e] : dummy, y.x);
                 acc_add<R, COMP>(s0[2 * e + 1], COMP ? c0[2 * e + 1] : dummy, y.y);
             }
             __syncthreads();
-        }
+        };
+        pair(0, BoolTag<true>{});
+        for (int r1 = 2; r1 < a.n; r1 += 2) pair(r1, BoolTag<false>{});
     }
 
     if (!valid) return;
