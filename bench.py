@@ -674,16 +674,48 @@ def run_3d(args, ctx, hd):
     fs = [inputs.hermitian_3d(L, rank_seed(ctx.rank, 4, a), dtype=np.complex64) for a in range(2)]
     f = [torch.from_numpy(x).to(ctx.dev) for x in fs]
     h = torch.empty_like(f[0])
-    plan = hd.Plan([L, L, L], [384, 384, 384], kind="hermitian")
-    clk = ClockSampler(ctx.local).start()
-    ms = ctx.max_over_ranks(ctx.time_it(lambda: plan.convolve(f, h, stream=ctx.stream), max(3, args.steps),
-                                        warm=args.warmup, label="timed"))
-    clocks = clk.stop()
     g = np.random.default_rng(1)
     pts = np.stack([g.integers(0, L, 16), g.integers(0, L, 16), g.integers(0, L // 2, 16)], 1)
     want = direct.convnd_points([x.astype(np.complex128) for x in fs], ("centered", "centered", "hermitian"), pts)
-    got = h.cpu().numpy()[tuple(pts.T)]
+
+    def rel(hh):
+        got = hh.cpu().numpy()[tuple(pts.T)]
+        return float(np.linalg.norm(got - want) / np.linalg.norm(want))
+
+    def time_plan(p_, label=None):
+        return ctx.max_over_ranks(ctx.time_it(lambda: p_.convolve(f, h, stream=ctx.stream), max(3, args.steps),
+                                              warm=args.warmup, label=label))
+
+    # parameters of the innermost (Hermitian) axis: cost model, then the learned selector (with the timed
+    # search as its fallback when the ensemble is unsure); outer axes: cost model
+    from paper_2303_17510_gb300 import selector
+    hd.tune_cache_clear()
+    hd.selector_clear()
+    with hd.Plan([L, L, L], [384, 384, 384], kind="hermitian") as pcm:
+        ms_cm = time_plan(pcm)
+        axes_cm = [pcm.axis_params(i) for i in range(3)]
+    models, _ = selector.train(selector.load_data(), k=4, steps=args.train_steps)
+    hd.selector_install(models, tau=0.05, sigma=0.25, fallback=True)
+    t0 = time.perf_counter()
+    plan = hd.Plan([L, L, L], [384, 384, 384], kind="hermitian")
+    plan_s = time.perf_counter() - t0
+    hd.selector_clear()
+    clk = ClockSampler(ctx.local).start()
+    ms = time_plan(plan, "timed")
+    clocks = clk.stop()
+    acc = rel(h)
     e2e = e2e_nd(ctx, plan, f, h)
+    axes = [plan.axis_params(i) for i in range(3)]
+    # the same parameters with compensated (TwoSum) residue sums in the inner convolutions
+    os.environ["HD_COMP"] = "1"
+    try:
+        pc = hd.Plan([L, L, L], [384, 384, 384], kind="hermitian", m=[a["m"] for a in axes],
+                     p=[a["p"] for a in axes], q=[a["q"] for a in axes])
+    finally:
+        del os.environ["HD_COMP"]
+    with pc:
+        ms_comp = time_plan(pc)
+        acc_comp = rel(h)
 
     def cufft():
         # explicit dealiasing of the same field: 384^3 real grid, inverse real FFTs, product, forward real FFT
@@ -700,12 +732,14 @@ def run_3d(args, ctx, hd):
     cu = ctx.time_it(cufft, 3)
     out = base_line(args, ctx, ctx.job_rate(1, ms), ms, "f32",
                     "synthetic (seeded real field, amplitude |k|^-5/3, exact Hermitian symmetry)",
-                    {"workload": WORKLOAD_NAMES["3d"], "axes": [plan.axis_params(i) for i in range(3)],
+                    {"workload": WORKLOAD_NAMES["3d"], "axes": axes, "planning_s": plan_s,
+                     "parameters": "innermost axis: learned selector (timed search when unsure); outer: cost model",
                      "scratch_bytes": plan.params()["scratch_bytes"],
                      "l2": "inputs+outputs 96 MiB; work buffers larger than L2"})
     out.update({"roofline": roofline(3 * L * L * (L // 2) * 8, ms, read_traffic("3d"), "3d plan (all kernels)"),
-                "accuracy": {"rel_l2_sampled": float(np.linalg.norm(got - want) / np.linalg.norm(want)),
-                             "points": len(pts)},
+                "accuracy": {"rel_l2_sampled": acc, "points": len(pts)},
+                "variants": {"cost_model_params": {"ms": ms_cm, "axes": axes_cm},
+                             "compensated_sums": {"ms": ms_comp, "rel_l2_sampled": acc_comp}},
                 "baselines": {"cufft_f32_explicit_384^3_real": {"value": 1e3 / cu, "unit": "conv/s", "ms": cu}},
                 "e2e": e2e, "clocks": clocks})
     if ctx.rank == 0 and not args.no_cpu_baseline:

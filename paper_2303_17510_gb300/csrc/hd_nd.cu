@@ -163,7 +163,18 @@ hd_status plan_create_nd(hd_plan** out, const hd_desc* d) {
                 ax.D = d->D[i] > 0 ? d->D[i] : (int)ax.n;
             }
         } else if (d->m[i] == 0) {
-            st = choose_axis(d->dtype, d->kind, d->mult, d->A, d->B, d->L[i], d->M[i], &ax);
+            // the innermost axis is a batch of 1D convolutions: tuning cache, selector, cost model
+            hd_desc d1;
+            std::memset(&d1, 0, sizeof(d1));
+            d1.ndim = 1;
+            d1.L[0] = d->L[i];
+            d1.M[0] = d->M[i];
+            d1.A = d->A;
+            d1.B = d->B;
+            d1.kind = d->kind;
+            d1.dtype = d->dtype;
+            d1.mult = d->mult;
+            st = auto_axis(&d1, &ax);
         } else {
             st = fill_axis(d->dtype, d->kind, d->mult, d->L[i], d->M[i], d->m[i], d->p[i], d->q[i], d->D[i], &ax);
         }

@@ -216,20 +216,46 @@ hd_status plan_finish(const hd_desc* d, const AxisPlan& ax, hd_plan** out) {
 
 }  // namespace
 
+// Axis parameters of a 1D description from a candidate (m, p, q, D, variant).
+hd_status axis_from_candidate(const hd_desc* d, const hd_candidate* c, AxisPlan* ax) {
+    hd_status st = fill_axis(d->dtype, d->kind, d->mult, d->L[0], d->M[0], c->m, c->p, c->q, c->D, ax);
+    if (st != HD_OK && st != HD_ERR_UNSUPPORTED) return st;
+    if (ax->S != c->S || ax->n != c->n) return HD_ERR_INVALID;
+    ax->comp = c->comp != 0 && d->dtype == HD_F32;
+    if (ax->path == PATH_FUSED) {
+        ax->E = c->E;
+        ax->minb = c->minb;
+        if (!fused_supported(d->dtype, d->kind, d->mult, ax->S, ax->nb, ax->Ls, ax->comp, ax->E, ax->minb))
+            return HD_ERR_UNSUPPORTED;
+    }
+    return HD_OK;
+}
+
+// Parameters of a 1D axis given with m = 0: the tuning cache, else the learned
+// selector (the timed search instead when it is unsure and its fallback is on),
+// else the cost model.  Also used for the innermost axis of N-D plans.
+hd_status auto_axis(const hd_desc* d, AxisPlan* ax) {
+    hd_candidate c;
+    if (cache_lookup(d, &c) && axis_from_candidate(d, &c, ax) == HD_OK) return HD_OK;
+    if (selector_installed()) {
+        std::vector<hd_candidate> cands;
+        enumerate_candidates(d, &cands);
+        std::vector<int> pick, conf;
+        if (!cands.empty() && selector_choose_batch({d}, {cands}, &pick, &conf) == HD_OK) {
+            c = cands[pick[0]];
+            if (!conf[0] && selector_fallback()) timed_choice(d, nullptr, &c);
+            if (axis_from_candidate(d, &c, ax) == HD_OK) return HD_OK;
+        }
+    }
+    return choose_axis(d->dtype, d->kind, d->mult, d->A, d->B, d->L[0], d->M[0], ax);
+}
+
 hd_status plan_create_from(hd_plan** out, const hd_desc* d, const hd_candidate* c) {
     hd_status st = check_desc_1d(d);
     if (st != HD_OK) return st;
     AxisPlan ax;
-    st = fill_axis(d->dtype, d->kind, d->mult, d->L[0], d->M[0], c->m, c->p, c->q, c->D, &ax);
-    if (st != HD_OK && st != HD_ERR_UNSUPPORTED) return st;
-    if (ax.S != c->S || ax.n != c->n) return HD_ERR_INVALID;
-    ax.comp = c->comp != 0 && d->dtype == HD_F32;
-    if (ax.path == PATH_FUSED) {
-        ax.E = c->E;
-        ax.minb = c->minb;
-        if (!fused_supported(d->dtype, d->kind, d->mult, ax.S, ax.nb, ax.Ls, ax.comp, ax.E, ax.minb))
-            return HD_ERR_UNSUPPORTED;
-    }
+    st = axis_from_candidate(d, c, &ax);
+    if (st != HD_OK) return st;
     return plan_finish(d, ax, out);
 }
 
@@ -237,22 +263,8 @@ hd_status plan_create(hd_plan** out, const hd_desc* d) {
     if (d->ndim == 2 || d->ndim == 3) return plan_create_nd(out, d);
     hd_status st = check_desc_1d(d);
     if (st != HD_OK) return st;
-    if (d->m[0] == 0) {
-        hd_candidate c;
-        if (cache_lookup(d, &c) && plan_create_from(out, d, &c) == HD_OK) return HD_OK;
-        if (selector_installed()) {
-            std::vector<hd_candidate> cands;
-            enumerate_candidates(d, &cands);
-            std::vector<int> pick, conf;
-            if (!cands.empty() && selector_choose_batch({d}, {cands}, &pick, &conf) == HD_OK) {
-                c = cands[pick[0]];
-                if (!conf[0] && selector_fallback()) timed_choice(d, nullptr, &c);
-                if (plan_create_from(out, d, &c) == HD_OK) return HD_OK;
-            }
-        }
-    }
     AxisPlan ax;
-    if (d->m[0] == 0) st = choose_axis(d->dtype, d->kind, d->mult, d->A, d->B, d->L[0], d->M[0], &ax);
+    if (d->m[0] == 0) st = auto_axis(d, &ax);
     else st = fill_axis(d->dtype, d->kind, d->mult, d->L[0], d->M[0], d->m[0], d->p[0], d->q[0], d->D[0], &ax);
     if (st != HD_OK) return st;
     if (d->D[0] > 0) ax.D = d->D[0];

@@ -73,17 +73,7 @@ struct hd_plan {
     void* scratch;     // split-path work buffer (chunk * A * n * S values)
     void* work[2];     // N-D: work buffer of each outer axis level
     int64_t inst_cap;  // N-D: outer instances per pass through the levels
-    hd::RaggedData* ragged;   // learned selector (hd_selector.cu)
-void selector_features(const hd_desc* d, const hd_candidate* c, float* f);
-bool selector_installed();
-int selector_fallback();
-hd_status selector_choose_batch(const std::vector<const hd_desc*>& descs,
-                                const std::vector<std::vector<hd_candidate>>& cands, std::vector<int>* pick,
-                                std::vector<int>* confident);
-// timed search for one description, keeping candidates accepted by `ok`
-hd_status timed_choice(const hd_desc* d, bool (*ok)(const hd_desc*, const hd_candidate&), hd_candidate* out);
-
-// ragged batch plans (hd_ragged.cu)
+    hd::RaggedData* ragged;   // ragged batch plans (hd_ragged.cu)
     int device;
     hd_status sticky;
 };
@@ -135,5 +125,8 @@ hd_status split_execute(const hd_plan& pl, const AxisPlan& ax, int64_t count, co
 
 // Legal, supported (m, p, q) of one axis chosen by the cost model; fills ax.
 hd_status choose_axis(int dtype, int kind, int mult, int A, int B, int64_t L, int64_t M, AxisPlan* ax);
+// Axis parameters of a 1D description with m = 0: tuning cache, learned selector
+// (timed search when unsure and allowed), cost model.
+hd_status auto_axis(const hd_desc* d, AxisPlan* ax);
 
 }  // namespace hd

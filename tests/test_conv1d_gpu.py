@@ -226,3 +226,57 @@ def test_plain_and_compensated_residue_sums(hd, monkeypatch, kind, comp):
             continue
         with plan:
             check(run_conv(hd, plan, fs), ref, "f32", False, (kind, comp, m, plan.params()))
+
+
+def test_persistent_bulk_copy_variant_matches_plain_kernel(hd):
+    """The persistent kernel (next batch element staged by bulk copies) and the
+    plain kernel run the same residue body: their outputs agree to FP32
+    rounding and both meet the FP32 bound.  A row that starts off a 16-byte
+    boundary (odd element offset) falls back to the plain kernel, whose output
+    it reproduces bit for bit."""
+    import os
+    import subprocess
+    import sys
+    import torch
+    L, M, count = 4096, 8191, 300
+    fs = make_inputs("complex", L, 2, count, 21)
+    best, cands = hd.autotune(count, reps=1, L=L, M=M)
+    pipe = [c for c in cands if c["minb"] == 1 and c["S"] <= 4096]
+    assert pipe, cands
+    ref = cdirect.conv1d_batch([f[[0, 150, 299]] for f in fs], L, "complex")
+    outs = []
+    for c in pipe[:2]:
+        with hd.Plan(L, M, candidate=c) as plan:
+            got = run_conv(hd, plan, fs)
+        check(got[[0, 150, 299]], ref, "f32", False, ("pipe", c))
+        outs.append(got)
+    # the same candidates with the persistent variant switched off, in a fresh process
+    code = (
+        "import sys, json, numpy as np, torch; sys.path.insert(0, '.');"
+        "import inputs, paper_2303_17510_gb300 as hd;"
+        f"L, M, count = {L}, {M}, {count};"
+        "fs = [inputs.uniform_complex((count, L), 21 + a) for a in range(2)];"
+        f"cands = {pipe[:2]!r};"
+        "res = [];\n"
+        "for c in cands:\n"
+        "    p = hd.Plan(L, M, candidate=c); d = [torch.from_numpy(f.astype(np.complex64)).cuda() for f in fs]\n"
+        "    o = torch.zeros_like(d[0]); p.convolve_batched(d, o, count, L); torch.cuda.synchronize()\n"
+        "    np.save(f'/tmp/hd_plain_{len(res)}.npy', o.cpu().numpy()); res.append(1); p.close()\n"
+    )
+    env = dict(os.environ, HD_PIPE="0")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    subprocess.run([sys.executable, "-c", code], cwd=root, env=env, check=True, timeout=300)
+    plains = [np.load(f"/tmp/hd_plain_{i}.npy") for i in range(len(outs))]
+    for i, got in enumerate(outs):
+        assert rel_l2(got, plains[i]) <= 1e-6, i
+    # a misaligned row start (one complex64 past a 16-byte boundary) takes the plain kernel
+    buf = [np.zeros((count * L + 1,), dtype=np.complex64) for _ in range(2)]
+    for a in range(2):
+        buf[a][1:] = fs[a].astype(np.complex64).ravel()
+    with hd.Plan(L, M, candidate=pipe[0]) as plan:
+        d = [torch.from_numpy(b).cuda() for b in buf]
+        out = torch.zeros(count * L + 1, dtype=torch.complex64, device="cuda")
+        plan.convolve_batched([x[1:] for x in d], out[1:], count, L)
+        torch.cuda.synchronize()
+        got = out[1:].cpu().numpy().reshape(count, L)
+    assert np.array_equal(got, plains[0])

@@ -112,3 +112,33 @@ def test_selector_gain_over_cost_model(hd):
         assert (pr["m"], pr["p"], pr["q"]) == (c["m"], c["p"], c["q"])
     finally:
         hd.selector_clear()
+
+
+def test_selector_picks_innermost_axis_of_nd_plans(hd):
+    """With a selector installed, the innermost axis of a 2D plan takes the
+    ensemble's choice for that axis's 1D problem, and the 2D result still
+    matches the oracle."""
+    import inputs
+    from oracle import direct
+    from paper_2303_17510_gb300 import selector
+    from tests.gpu_util import rel_l2, to_dev
+    import torch
+    models, _ = selector.train(selector.load_data(), k=2, steps=300)
+    hd.tune_cache_clear()
+    selector.b.selector_install(models, tau=0.0, sigma=1e9, fallback=False)
+    try:
+        Lx, Ly = 24, 600
+        My = 2 * Ly - 1 + 5
+        c, conf = hd.selector_choose(L=Ly, M=My)
+        assert conf == 1
+        fs = [inputs.uniform_complex((Lx, Ly), 61 + a) for a in range(2)]
+        with hd.Plan([Lx, Ly], [2 * Lx - 1, My]) as plan:
+            ax = plan.axis_params(1)
+            assert (ax["m"], ax["p"], ax["q"], ax["S"], ax["n"]) == (c["m"], c["p"], c["q"], c["S"], c["n"])
+            d = [to_dev(f, "f32") for f in fs]
+            out = torch.zeros_like(d[0])
+            plan.convolve(d, out)
+            torch.cuda.synchronize()
+        assert rel_l2(out.cpu().numpy(), direct.convnd(fs, ("complex", "complex"))) <= 1e-5
+    finally:
+        hd.selector_clear()
