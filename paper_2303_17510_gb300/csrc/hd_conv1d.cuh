@@ -121,10 +121,17 @@ struct ConvLaunch {
 // same sequence of barriers (groups of one CTA share n).  FFT twiddles are
 // read through the read-only data cache (a shared-memory table measured
 // slower: it competes with the exchanges for shared-memory bandwidth).
+struct NoHook {
+    __device__ __forceinline__ void operator()() const {}
+};
+
 // STAGE = false: the inputs are already in st (staged by bulk copies).
-template <class R, int S, int E, int KIND, int MULT, int NB, bool COMP, bool STAGE = true>
+// consumed(): called by every thread once the staged inputs are no longer
+// read (after the forward transforms of the last residue, whose exchanges
+// put barriers after the last reads of st).
+template <class R, int S, int E, int KIND, int MULT, int NB, bool COMP, bool STAGE = true, class Hook = NoHook>
 __device__ __forceinline__ void conv1d_body(const ConvArgs& a, int64_t inst, bool valid, int tau, cplx<R>* st,
-                                            cplx<R>* sm) {
+                                            cplx<R>* sm, const Hook& consumed = Hook{}) {
     using T = cplx<R>;
     using Sh = FftShape<S, E>;
     constexpr int TT = Sh::T;
@@ -190,6 +197,7 @@ __device__ __forceinline__ void conv1d_body(const ConvArgs& a, int64_t inst, boo
                 }
             }
             fft_forward<S, E, A>(v, sm, twS, tau);
+            if (r == a.n - 1) consumed();
             T p[E];
 #pragma unroll
             for (int e = 0; e < E; ++e) {
@@ -241,6 +249,7 @@ __device__ __forceinline__ void conv1d_body(const ConvArgs& a, int64_t inst, boo
                 }
             }
             fft_forward<S, E, A>(v, sm, twS, tau);
+            if (r1 + 2 >= a.n) consumed();
             // real parts carry residue r1, imaginary parts residue r2
             T p[E];
 #pragma unroll
@@ -386,8 +395,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     return true;
 }
 
-template <class R, int S, int E, int KIND, int MULT, int NB, bool COMP>
-__global__ void __launch_bounds__(ConvLaunch<S, E>::MAXT, 1) conv1d_kernel_pipe(const __grid_constant__ ConvArgs a) {
+// NBUF = 2: the next step is staged into the second buffer while the CTA
+// computes (one CTA per SM).  NBUF = 1: one buffer, released early: the copy
+// for the next step starts once the last residue's forward transforms have
+// consumed the staged inputs, and overlaps that residue's product, inverse
+// transform and accumulation (keeps two CTAs per SM).
+template <class R, int S, int E, int KIND, int MULT, int NB, bool COMP, int MINB, int NBUF>
+__global__ void __launch_bounds__(ConvLaunch<S, E>::MAXT, MINB) conv1d_kernel_pipe(const __grid_constant__ ConvArgs a) {
     using T = cplx<R>;
     using Sh = FftShape<S, E>;
     constexpr int TT = Sh::T;
@@ -400,7 +414,7 @@ __global__ void __launch_bounds__(ConvLaunch<S, E>::MAXT, 1) conv1d_kernel_pipe(
     const int tau = threadIdx.x - g * TT;
     const size_t stage_elems = (size_t)G * A * a.ls_pad;          // one staging buffer (all groups)
     T* stage0 = reinterpret_cast<T*>(smem_raw);
-    T* sm = stage0 + 2 * stage_elems + (size_t)g * A * Sh::SMEM;
+    T* sm = stage0 + NBUF * stage_elems + (size_t)g * A * Sh::SMEM;
     const int64_t nsteps = (a.count + G - 1) / G;                    // CTA steps over the batch
     const uint32_t row_bytes = (uint32_t)(a.Ls * sizeof(T));
 
@@ -430,22 +444,31 @@ __global__ void __launch_bounds__(ConvLaunch<S, E>::MAXT, 1) conv1d_kernel_pipe(
     if (k >= nsteps) return;
     if (threadIdx.x == 0) issue(k, 0);
     for (int it = 0; k < nsteps; ++it, k += gridDim.x) {
-        const int b = it & 1;
+        const int b = NBUF == 2 ? (it & 1) : 0;
+        const uint32_t parity = NBUF == 2 ? (uint32_t)((it >> 1) & 1) : (uint32_t)(it & 1);
         const int64_t kn = k + gridDim.x;
-        if (threadIdx.x == 0 && kn < nsteps) issue(kn, b ^ 1);   // buffer b^1 was released by the last barrier
-        if (threadIdx.x == 0) s_ok = mbar_wait(&bar[b], (uint32_t)((it >> 1) & 1)) ? 1 : 0;
+        if (NBUF == 2 && threadIdx.x == 0 && kn < nsteps) issue(kn, b ^ 1);   // released by the last barrier
+        if (threadIdx.x == 0) s_ok = mbar_wait(&bar[b], parity) ? 1 : 0;
         __syncthreads();
         if (!s_ok) {
             if (threadIdx.x == 0) {
                 if (a.err) atomicExch(a.err, 1);
-                if (kn < nsteps) mbar_wait(&bar[b ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
+                if (NBUF == 2 && kn < nsteps) mbar_wait(&bar[b ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
             }
             return;
         }
-        mbar_try(&bar[b], (uint32_t)((it >> 1) & 1));                // this thread's own acquire of the phase
+        mbar_try(&bar[b], parity);                                   // this thread's own acquire of the phase
         const int64_t inst = k * G + g;
-        conv1d_body<R, S, E, KIND, MULT, NB, COMP, false>(a, inst, inst < a.count, tau,
-                                                          stage0 + b * stage_elems + (size_t)g * A * a.ls_pad, sm);
+        T* st = stage0 + b * stage_elems + (size_t)g * A * a.ls_pad;
+        if constexpr (NBUF == 2) {
+            conv1d_body<R, S, E, KIND, MULT, NB, COMP, false>(a, inst, inst < a.count, tau, st, sm);
+        } else {
+            auto release = [&]() {
+                __syncthreads();                                     // every thread is past its last read of st
+                if (threadIdx.x == 0 && kn < nsteps) issue(kn, 0);
+            };
+            conv1d_body<R, S, E, KIND, MULT, NB, COMP, false>(a, inst, inst < a.count, tau, st, sm, release);
+        }
         __syncthreads();
     }
 }

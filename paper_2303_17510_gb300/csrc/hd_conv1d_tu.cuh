@@ -45,13 +45,16 @@ int* pipe_err_ptr() {
     return ptrs[dev];
 }
 
-// Persistent CTAs with bulk-copy staging (conv1d_kernel_pipe): for the
-// one-CTA-per-SM variants, when both staging buffers fit and every row is a
-// whole number of 16-byte units on a 16-byte boundary.  HD_PIPE=0 turns it off.
-template <class R, int S, int E, int KIND, int MULT, int NB, bool COMP>
+// Persistent CTAs with bulk-copy staging (conv1d_kernel_pipe), when every row
+// is a whole number of 16-byte units on a 16-byte boundary: the one-CTA-per-SM
+// variants stage the next step into a second buffer (when both fit), the
+// two-CTA variants release their single buffer early (when two CTAs still fit
+// per SM).  HD_PIPE=0 turns the persistent kernels off.
+template <class R, int S, int E, int KIND, int MULT, int NB, bool COMP, int MINB>
 cudaError_t launch_pipe(const ConvArgs& a0, cudaStream_t st, bool* used) {
     constexpr int T = S / E;
     constexpr int A = MULT == MULT_PRODUCT ? 2 : 3;
+    constexpr int NBUF = MINB == 1 ? 2 : 1;
     *used = false;
     static const bool enabled = [] {
         const char* e = std::getenv("HD_PIPE");
@@ -66,10 +69,10 @@ cudaError_t launch_pipe(const ConvArgs& a0, cudaStream_t st, bool* used) {
     if (G < 1) G = 1;
     const size_t fft = size_t(A) * FftShape<S, E>::SMEM * esz;
     const size_t stg = size_t(A) * a0.ls_pad * esz;
-    while (G > 1 && G * (2 * stg + fft) > kMaxSmemPerBlock - 64) --G;
-    const size_t smem = size_t(G) * (2 * stg + fft);
+    while (G > 1 && G * (NBUF * stg + fft) > kMaxSmemPerBlock - 64) --G;
+    const size_t smem = size_t(G) * (NBUF * stg + fft);
     if (smem > kMaxSmemPerBlock - 64) return cudaSuccess;
-    auto k = conv1d_kernel_pipe<R, S, E, KIND, MULT, NB, COMP>;
+    auto k = conv1d_kernel_pipe<R, S, E, KIND, MULT, NB, COMP, MINB, NBUF>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -78,7 +81,7 @@ cudaError_t launch_pipe(const ConvArgs& a0, cudaStream_t st, bool* used) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, G * T, smem) != cudaSuccess || per < 1) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, G * T, smem) != cudaSuccess || per < MINB) {
         cudaGetLastError();
         return cudaSuccess;
     }
@@ -98,9 +101,12 @@ cudaError_t launch_pipe(const ConvArgs& a0, cudaStream_t st, bool* used) {
 template <class R, int S, int E, int KIND, int MULT, int NB, bool COMP, int MINB>
 cudaError_t launch_one(const ConvArgs& a, cudaStream_t st) {
     constexpr int T = S / E;
-    if constexpr (MINB == 1) {
+    // one convolution per CTA step (T >= 256) and plain sums: with smaller transforms the per-step
+    // compute is too short to hide a copy (measured slower), and compensated sums (many residues)
+    // are rare; both keep the plain kernel, which also bounds the instantiations
+    if constexpr (!COMP && T >= 256) {
         bool used = false;
-        cudaError_t e = launch_pipe<R, S, E, KIND, MULT, NB, COMP>(a, st, &used);
+        cudaError_t e = launch_pipe<R, S, E, KIND, MULT, NB, COMP, MINB>(a, st, &used);
         if (used || e != cudaSuccess) return e;
     }
     const int G = groups_for<R, S, E, MULT>(a.ls_pad);
