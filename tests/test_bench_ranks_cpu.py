@@ -69,3 +69,23 @@ def test_reference_arm_only_rank0_prints(monkeypatch):
     with redirect_stdout(buf):
         bench.run_reference(args)
     assert buf.getvalue() == ""
+
+
+def test_reference_arm_json_line(monkeypatch, capsys):
+    """The reference arm (the FP64 oracle on the host cores) prints one JSON
+    line with the contract's keys, its own cpu_baseline and a zero-copy e2e."""
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("RANK", "0")
+    args = type("A", (), dict(steps=1, warmup=3, gpus=1, workload="single64", ragged_n=10000))()
+    bench.run_reference(args)
+    line = capsys.readouterr().out.strip().splitlines()
+    assert len(line) == 1
+    d = json.loads(line[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    assert d["config"]["workload"] == "1d_single_L1024_M2047_f64"
