@@ -420,7 +420,7 @@ def run_batch1d(args, ctx, hd):
     # The batch is cut into chunks that rotate over NS streams (one plan per stream and sub-config), so
     # the host->device copy of one chunk, the convolutions of another and the device->host copy of a
     # third overlap; the timed region waits for every stream.
-    NS, NCH = 3, 8
+    NS, NCH = args.e2e_streams, args.e2e_chunks
     csz = (COUNT + NCH - 1) // NCH
     h_in = [[fin[si][a].cpu().pin_memory() for a in range(2)] for si in range(len(SUBS))]
     h_out = [torch.empty((COUNT, L1D), dtype=torch.complex64).pin_memory() for _ in SUBS]
@@ -878,6 +878,8 @@ def main():
     ap.add_argument("--m", type=str, default="auto", help="batch1d: m per sub-config, e.g. 2048,4096")
     ap.add_argument("--count", type=int, default=4096, help="batch1d: batch size per sub-config")
     ap.add_argument("--ragged-n", type=int, default=10000)
+    ap.add_argument("--e2e-streams", type=int, default=3, help="batch1d e2e: streams the chunks rotate over")
+    ap.add_argument("--e2e-chunks", type=int, default=8, help="batch1d e2e: chunks per sub-config")
     ap.add_argument("--train-steps", type=int, default=2000)
     ap.add_argument("--exhaustive", action="store_true", help="ragged: also time the per-instance exhaustive search")
     args = ap.parse_args()
