@@ -44,8 +44,10 @@ struct ColShape {
     static constexpr int THREADS = T * TY;
 };
 
-// Forward: fold + twist of residue r0 + blockIdx.y % nr of input blockIdx.y / nr,
-// FFT along x, spectral values to the work buffer.
+// Forward: input blockIdx.y, all nr residues of the block: the column tile is
+// read once (both folded blocks kept in registers), then per residue fold +
+// twist, FFT along x, spectral values to the work buffer.  Residue 0 (r0 = 0)
+// has unit twists.
 template <class R, int S, int E, int KIND>
 __global__ void __launch_bounds__(ColShape<S, E>::THREADS) col_forward(const __grid_constant__ ColArgs a) {
     using T = cplx<R>;
@@ -57,37 +59,48 @@ __global__ void __launch_bounds__(ColShape<S, E>::THREADS) col_forward(const __g
     const int tau = threadIdx.x / TY;
     const int64_t col = (int64_t)blockIdx.x * TY + y;
     const bool valid = col < a.ncols;
-    const int rr = blockIdx.y % a.nr;
-    const int aa = blockIdx.y / a.nr;
-    const int r = a.r0 + rr;
+    const int aa = blockIdx.y;
     const int64_t inst = blockIdx.z;
     T* sm = reinterpret_cast<T*>(smem_raw) + y;
     const TwGlobal<T> tw{static_cast<const T*>(a.twS)};
     const T* twN = static_cast<const T*>(a.twN);
     const T* f = static_cast<const T*>(a.f[aa]) + inst * a.inst_stride + (valid ? col : 0);
-    T cr = ldtw(twN + (int64_t)a.n * S + r);
-    if constexpr (KIND == KIND_CENTERED) cr = cconj(cr);
-    T v[E];
+    T b0[E], b1[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         const int j = tau + TT * e;
-        T b0 = czero<T>(), b1 = czero<T>();
+        b0[e] = czero<T>();
+        b1[e] = czero<T>();
         if (valid) {
             if constexpr (KIND == KIND_COMPLEX) {
-                if (j < a.L) b0 = f[(int64_t)j * a.pitch];
-                if (j + S < a.L) b1 = f[(int64_t)(j + S) * a.pitch];
+                if (j < a.L) b0[e] = f[(int64_t)j * a.pitch];
+                if (j + S < a.L) b1[e] = f[(int64_t)(j + S) * a.pitch];
             } else {
-                if (j < a.L - a.H) b0 = f[(int64_t)(j + a.H) * a.pitch];
-                if (j >= S - a.H) b1 = f[(int64_t)(j - S + a.H) * a.pitch];
+                if (j < a.L - a.H) b0[e] = f[(int64_t)(j + a.H) * a.pitch];
+                if (j >= S - a.H) b1[e] = f[(int64_t)(j - S + a.H) * a.pitch];
             }
         }
-        v[e] = cmul(cadd(b0, cmul(cr, b1)), ldtw(twN + (int64_t)r * S + j));
     }
-    fft_forward<S, E, 1, TY>(v, sm, tw, tau);
-    if (!valid) return;
-    T* w = static_cast<T*>(a.work) + (((int64_t)aa * a.count + inst) * a.nr + rr) * (int64_t)S * a.ncols + col;
+    for (int rr = 0; rr < a.nr; ++rr) {
+        const int r = a.r0 + rr;
+        T v[E];
+        if (r == 0) {
 #pragma unroll
-    for (int e = 0; e < E; ++e) w[(int64_t)(tau + TT * e) * a.ncols] = v[e];
+            for (int e = 0; e < E; ++e) v[e] = cadd(b0[e], b1[e]);
+        } else {
+            T cr = ldtw(twN + (int64_t)a.n * S + r);
+            if constexpr (KIND == KIND_CENTERED) cr = cconj(cr);
+#pragma unroll
+            for (int e = 0; e < E; ++e)
+                v[e] = cmul(cadd(b0[e], cmul(cr, b1[e])), ldtw(twN + (int64_t)r * S + tau + TT * e));
+        }
+        fft_forward<S, E, 1, TY>(v, sm, tw, tau);
+        if (valid) {
+            T* w = static_cast<T*>(a.work) + (((int64_t)aa * a.count + inst) * a.nr + rr) * (int64_t)S * a.ncols + col;
+#pragma unroll
+            for (int e = 0; e < E; ++e) w[(int64_t)(tau + TT * e) * a.ncols] = v[e];
+        }
+    }
 }
 
 // Backward: for every residue of the block, inverse FFT along x of the
@@ -124,13 +137,14 @@ __global__ void __launch_bounds__(ColShape<S, E>::THREADS) col_backward(const __
 #pragma unroll
         for (int e = 0; e < E; ++e) v[e] = valid ? g[(int64_t)(tau + TT * e) * a.ncols] : czero<T>();
         fft_inverse<S, E, 1, TY>(v, sm, tw, tau);
+        const bool r0 = r == 0;   // unit twists
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             const int j = tau + TT * e;
-            const T yv = cmulc(v[e], ldtw(twN + (int64_t)r * S + j));
+            const T yv = r0 ? v[e] : cmulc(v[e], ldtw(twN + (int64_t)r * S + j));
             acc_add<R, COMP>(s0[2 * e], COMP ? c0[2 * e] : dummy, yv.x);
             acc_add<R, COMP>(s0[2 * e + 1], COMP ? c0[2 * e + 1] : dummy, yv.y);
-            const T y1 = cmulc(yv, cr);
+            const T y1 = r0 ? yv : cmulc(yv, cr);
             acc_add<R, COMP>(s1[2 * e], COMP ? c1[2 * e] : dummy, y1.x);
             acc_add<R, COMP>(s1[2 * e + 1], COMP ? c1[2 * e + 1] : dummy, y1.y);
         }

@@ -27,7 +27,7 @@ cudaError_t col_run(const ColArgs& a, cudaStream_t st) {
             cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
         }
-        k<<<dim3(gx, (unsigned)(a.A * a.nr), (unsigned)a.count), CS::THREADS, smem, st>>>(a);
+        k<<<dim3(gx, (unsigned)a.A, (unsigned)a.count), CS::THREADS, smem, st>>>(a);
     } else {
         auto k = col_backward<R, S, E, KIND, COMP>;
         if (smem > 48 * 1024) {
