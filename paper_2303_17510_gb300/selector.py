@@ -8,6 +8,7 @@ and drives the loops.
 
 Run as a script on a GPU to regenerate the committed training set:
     python -m paper_2303_17510_gb300.selector --out paper_2303_17510_gb300/data/selector_gb300.json
+    python -m paper_2303_17510_gb300.selector --append --kind hermitian --problems 120 --seed 7 --L-hi 8192
 """
 from __future__ import annotations
 
@@ -25,19 +26,21 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 DATA = os.path.join(HERE, "data", "selector_gb300.json")
 
 
-def problem_set(n, seed, L_lo=64, L_hi=65536, ratio_lo=0.3, ratio_hi=0.67):
+def problem_set(n, seed, L_lo=64, L_hi=65536, ratio_lo=0.3, ratio_hi=0.67, kind=None):
     """Random 1D FP32 problems of the ragged workload's distribution: L
     log-uniform, L/M uniform, A in {2, 3}; ratios above 1/2 use the centered
-    kind and M is raised to the kind's dealiasing bound when needed."""
+    kind and M is raised to the kind's dealiasing bound when needed.  `kind`
+    forces one kind for every problem (e.g. "hermitian", the innermost axis
+    of Hermitian N-D data)."""
     g = np.random.default_rng(seed)
     out = []
     for _ in range(n):
         L = int(math.floor(math.exp(g.uniform(math.log(L_lo), math.log(L_hi)))))
         r = float(g.uniform(ratio_lo, ratio_hi))
         A = 2 if g.uniform() < 0.5 else 3
-        kind = "centered" if r > 0.5 else "complex"
-        M = max(int(math.ceil(L / r)), b.dealias_bound(kind, L, "product" if A == 2 else "sum_pairs3"))
-        out.append(dict(L=L, M=M, A=A, kind=kind))
+        k = kind or ("centered" if r > 0.5 else "complex")
+        M = max(int(math.ceil(L / r)), b.dealias_bound(k, L, "product" if A == 2 else "sum_pairs3"))
+        out.append(dict(L=L, M=M, A=A, kind=k))
     return out
 
 
@@ -146,16 +149,29 @@ def load_data(path=DATA):
                 pid=np.asarray(d["pid"], np.int64), cands=d["cands"], problems=d["problems"])
 
 
+def merge_data(a, c):
+    """Training sets a and c as one (problem indices of c shifted past a's)."""
+    off = len(a["problems"])
+    return dict(X=np.concatenate([a["X"], c["X"]]), y=np.concatenate([a["y"], c["y"]]),
+                pid=np.concatenate([a["pid"], c["pid"] + off]), cands=list(a["cands"]) + list(c["cands"]),
+                problems=list(a["problems"]) + list(c["problems"]))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=DATA)
     ap.add_argument("--problems", type=int, default=400)
     ap.add_argument("--seed", type=int, default=123)
+    ap.add_argument("--kind", default=None, help="one kind for every problem (default: the ragged mix)")
+    ap.add_argument("--L-hi", type=int, default=65536)
+    ap.add_argument("--append", action="store_true", help="add the new problems to the existing set in --out")
     args = ap.parse_args()
-    data = collect(problem_set(args.problems, args.seed))
+    data = collect(problem_set(args.problems, args.seed, L_hi=args.L_hi, kind=args.kind))
+    if args.append and os.path.exists(args.out):
+        data = merge_data(load_data(args.out), data)
     os.makedirs(os.path.dirname(args.out), exist_ok=True)
     save_data(data, args.out)
-    print("rows", len(data["y"]), "problems", args.problems)
+    print("rows", len(data["y"]), "problems", len(data["problems"]))
 
 
 if __name__ == "__main__":
