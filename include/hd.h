@@ -327,6 +327,15 @@ hd_status hd_ragged_inject_stall(hd_plan* plan, int64_t i);
 hd_status hd_convolve_batched_noalloc(const hd_plan* plan, int64_t count, const void* const* f, void* const* h,
                                       int64_t batch_stride, void* stream);
 
+/* Synchronizes the current device and reports whether any persistent
+ * batched kernel launched on it since the last call had a bounded wait on its
+ * staging copies run out (HD_ERR_TIMEOUT; the affected batch elements are not
+ * computed), HD_ERR_CUDA on a device error, HD_OK otherwise.  Clears the
+ * report.  (No counterpart in the paper: the persistent kernels stage their
+ * inputs with asynchronous bulk copies whose completion they wait for with a
+ * time limit.) */
+hd_status hd_device_status(void);
+
 /* Releases the plan's device memory (after synchronizing its device). NULL ok. */
 hd_status hd_plan_destroy(hd_plan* plan);
 

@@ -75,6 +75,7 @@ _sig("hd_plan_get_axis_params", ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER
                                                ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_i64),
                                                ctypes.POINTER(_i64)])
 _sig("hd_plan_destroy", ctypes.c_int, [_vp])
+_sig("hd_device_status", ctypes.c_int, [])
 _sig("hd_enumerate_candidates", ctypes.c_int, [ctypes.POINTER(hd_desc), ctypes.POINTER(hd_candidate), ctypes.c_int,
                                                ctypes.POINTER(ctypes.c_int)])
 _sig("hd_autotune", ctypes.c_int, [ctypes.POINTER(hd_desc), _i64, ctypes.c_int, ctypes.POINTER(hd_candidate),
@@ -115,6 +116,12 @@ _sig("hd_ragged_inject_stall", ctypes.c_int, [_vp, _i64])
 def _check(rc, where):
     if rc != 0:
         raise HdError(rc, where)
+
+
+def device_status() -> str:
+    """Synchronizes the current device; "HD_ERR_TIMEOUT" if a persistent batched
+    kernel's bounded wait ran out since the last call, else "HD_OK"."""
+    return STATUS[lib.hd_device_status()]
 
 
 def status_string(code: int) -> str:

@@ -257,6 +257,22 @@ cudaError_t forward_residue_launch(const Conv1dCfg& c, const ConvArgs& a, int r,
 
 extern "C" {
 
+hd_status hd_device_status(void) {
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        cudaGetLastError();
+        return HD_ERR_CUDA;
+    }
+    const int e[6] = {conv1d_take_error_f32_complex(), conv1d_take_error_f32_centered(),
+                      conv1d_take_error_f32_hermitian(), conv1d_take_error_f64_complex(),
+                      conv1d_take_error_f64_centered(), conv1d_take_error_f64_hermitian()};
+    hd_status st = HD_OK;
+    for (int v : e) {
+        if (v < 0) return HD_ERR_CUDA;
+        if (v > 0) st = HD_ERR_TIMEOUT;
+    }
+    return st;
+}
+
 const char* hd_status_string(hd_status s) {
     switch (s) {
         case HD_OK: return "HD_OK";

@@ -30,7 +30,8 @@
 // imaginary parts separately; the inverse of the product splits back by
 // y_j = (Y_j + conj Y_{S-j})/2 and (Y_j - conj Y_{S-j})/(2i).
 //
-// FP32 accumulation over residues is compensated (TwoSum); FP64 is plain.
+// FP32 accumulation over residues is compensated (TwoSum) from 8 residues on
+// (COMP), plain below; FP64 is plain.
 #pragma once
 
 #include "hd_fft.cuh"

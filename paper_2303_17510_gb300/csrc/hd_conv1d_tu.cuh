@@ -203,4 +203,17 @@ int HD_FN(conv1d_variants_, HD_DT, HD_KN)(Conv1dCfg* out, int cap) {
     return n;
 }
 
+// Reads and clears this unit's error word on the current device (after the
+// caller synchronized it): 1 if a bounded wait ran out, 0 if not, -1 on error.
+int HD_FN(conv1d_take_error_, HD_DT, HD_KN)() {
+    int v = 0;
+    const int zero = 0;
+    if (cudaMemcpyFromSymbol(&v, g_pipe_err, sizeof(int)) != cudaSuccess ||
+        cudaMemcpyToSymbol(g_pipe_err, &zero, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    return v != 0 ? 1 : 0;
+}
+
 }  // namespace hd

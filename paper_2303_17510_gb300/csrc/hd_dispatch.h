@@ -50,7 +50,8 @@ int col_E_of_f64(int S);
     cudaError_t conv1d_launch_##DT##_##KN(const Conv1dCfg& c, const ConvArgs& a, cudaStream_t st);            \
     cudaError_t forward_residue_launch_##DT##_##KN(const Conv1dCfg& c, const ConvArgs& a, int r, int m,       \
                                                     void* out, cudaStream_t st);                              \
-    int conv1d_variants_##DT##_##KN(Conv1dCfg* out, int cap);
+    int conv1d_variants_##DT##_##KN(Conv1dCfg* out, int cap);                                                \
+    int conv1d_take_error_##DT##_##KN();
 HD_DECL_TU(f32, complex)
 HD_DECL_TU(f32, centered)
 HD_DECL_TU(f32, hermitian)

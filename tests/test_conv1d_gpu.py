@@ -280,3 +280,4 @@ def test_persistent_bulk_copy_variant_matches_plain_kernel(hd):
         torch.cuda.synchronize()
         got = out[1:].cpu().numpy().reshape(count, L)
     assert np.array_equal(got, plains[0])
+    assert hd.device_status() == "HD_OK"     # no bounded wait of the persistent kernels ran out
