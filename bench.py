@@ -649,6 +649,8 @@ def run_2d(args, ctx, hd):
                 "baselines": {"fp64_hybrid": {"value": 1e3 / res["f64"]["ms"], "unit": "conv/s",
                                               "rel_l2_sampled": res["f64"]["rel_l2_sampled"]},
                               "cufft_f32_explicit_4096x4096": {"value": 1e3 / cu, "unit": "conv/s", "ms": cu}},
+                # one convolution: outer-axis forward, the inner batch of rows, outer-axis backward
+                "gpu_launches": 3 * max(3, args.steps),
                 "e2e": e2e, "clocks": res["f32"]["clocks"]})
     if ctx.rank == 0 and not args.no_cpu_baseline:
         rate, nt, sample = oracle_rate_nd("2d")
@@ -750,6 +752,8 @@ def run_3d(args, ctx, hd):
                 "variants": {"cost_model_params": {"ms": ms_cm, "axes": axes_cm},
                              "compensated_sums": {"ms": ms_comp, "rel_l2_sampled": acc_comp}},
                 "baselines": {"cufft_f32_explicit_384^3_real": {"value": 1e3 / cu, "unit": "conv/s", "ms": cu}},
+                # one convolution: two outer-axis forward kernels, the inner batch, two outer-axis backward
+                "gpu_launches": 5 * max(3, args.steps),
                 "e2e": e2e, "clocks": clocks})
     if ctx.rank == 0 and not args.no_cpu_baseline:
         rate, nt, sample = oracle_rate_nd("3d")
