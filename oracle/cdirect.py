@@ -21,11 +21,17 @@ MULT = {"product": 0, "sum_pairs3": 1}
 
 
 def build(force: bool = False) -> str:
+    import fcntl
     os.makedirs(os.path.dirname(_OUT), exist_ok=True)
-    if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
-        tmp = _OUT + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread", _SRC, "-o", tmp])
-        os.replace(tmp, _OUT)
+    with open(os.path.join(os.path.dirname(_OUT), ".lock"), "w") as lk:
+        fcntl.flock(lk, fcntl.LOCK_EX)   # one builder at a time (several processes may call this)
+        try:
+            if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
+                tmp = _OUT + f".tmp{os.getpid()}"
+                subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread", _SRC, "-o", tmp])
+                os.replace(tmp, _OUT)
+        finally:
+            fcntl.flock(lk, fcntl.LOCK_UN)
     return _OUT
 
 

@@ -69,7 +69,19 @@ def _compile(src: str, hdr: str, extra) -> str:
 
 
 def build(verbose: bool = False, jobs: int | None = None, extra=None) -> str:
+    """Builds (or reuses) libhd.so; concurrent callers (one per rank) are
+    serialized by a file lock, so only the first compiles."""
     os.makedirs(OUT_DIR, exist_ok=True)
+    import fcntl
+    with open(os.path.join(OUT_DIR, ".lock"), "w") as lk:
+        fcntl.flock(lk, fcntl.LOCK_EX)
+        try:
+            return _build_locked(verbose, jobs, extra)
+        finally:
+            fcntl.flock(lk, fcntl.LOCK_UN)
+
+
+def _build_locked(verbose, jobs, extra) -> str:
     extra = list(extra or [])
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     hdr = ""
