@@ -228,8 +228,9 @@ struct FftShape {
     // sub-transform size before pass k
     __host__ __device__ static constexpr int sub(int k) { return k == 0 ? S : sub(k - 1) / radix(k - 1); }
     static constexpr int RLAST = radix(K - 1);
-    // padded shared elements for one transform
-    static constexpr int SMEM = S + S / 16;
+    // padded shared elements for one transform: up to 2 pad elements per 16
+    // (see fft_exchange) for E = 8, 1 per 16 otherwise
+    static constexpr int SMEM = S + (E == 8 ? S / 8 : S / 16);
     // Twiddle table layout: pass k (with Q_k > 1) stores zeta_{N_k}^{c k1} at
     // tw_offset(k) + (k1 - 1) Q_k + c, so lanes with consecutive c read
     // consecutive entries.
@@ -306,14 +307,21 @@ __device__ __forceinline__ void fft_exchange(T* v, T* sm, int tau) {
     constexpr int V = S / R;
     constexpr int Rn = Sh::radix(k + 1);
     constexpr int Qn = Sh::sub(k + 1) / Rn;
+    // Pad elements per 16: 1, or 2 for the radix-8 reads with 1 < Qn < 16, whose
+    // half-warps otherwise meet two words in one bank (checked on the CPU for
+    // every exchange of E = 8 and 16: the writes and reads of each exchange
+    // are then conflict-free).  Column tiles (CST > 1) keep 1.
+    constexpr int PADM = (CST == 1 && Rn == 8 && Qn > 1 && Qn < 16) ? 2 : 1;
+    static_assert(PADM == 1 || E == 8, "two pad elements per 16 only fit the E = 8 buffers");
+    auto padk = [](int a) { return a + (a >> 4) * PADM; };
     if constexpr (FWD) {
 #pragma unroll
         for (int beta = 0; beta < E / R; ++beta) {
             const int nu = tau + Sh::T * beta;
-            const int pn = padidx(nu);
+            const int pn = padk(nu);
 #pragma unroll
             for (int k1 = 0; k1 < R; ++k1) {
-                const int idx = (V % 16 == 0) ? pn + V * k1 + (V / 16) * k1 : padidx(nu + V * k1);
+                const int idx = (V % 16 == 0) ? pn + V * k1 + (V / 16) * PADM * k1 : padk(nu + V * k1);
 #pragma unroll
                 for (int a = 0; a < NA; ++a) sm[(a * Sh::SMEM + idx) * CST] = v[a * E + beta * R + k1];
             }
@@ -324,10 +332,10 @@ __device__ __forceinline__ void fft_exchange(T* v, T* sm, int tau) {
             const int nu = tau + Sh::T * beta;
             const int b = nu / Qn, c = nu & (Qn - 1);
             const int base = b * Rn * Qn + c;
-            const int pb = padidx(base);
+            const int pb = padk(base);
 #pragma unroll
             for (int i = 0; i < Rn; ++i) {
-                const int idx = (Qn % 16 == 0) ? pb + i * Qn + (Qn / 16) * i : padidx(base + i * Qn);
+                const int idx = (Qn % 16 == 0) ? pb + i * Qn + (Qn / 16) * PADM * i : padk(base + i * Qn);
 #pragma unroll
                 for (int a = 0; a < NA; ++a) v[a * E + beta * Rn + i] = sm[(a * Sh::SMEM + idx) * CST];
             }
@@ -339,10 +347,10 @@ __device__ __forceinline__ void fft_exchange(T* v, T* sm, int tau) {
             const int nu = tau + Sh::T * beta;
             const int b = nu / Qn, c = nu & (Qn - 1);
             const int base = b * Rn * Qn + c;
-            const int pb = padidx(base);
+            const int pb = padk(base);
 #pragma unroll
             for (int i = 0; i < Rn; ++i) {
-                const int idx = (Qn % 16 == 0) ? pb + i * Qn + (Qn / 16) * i : padidx(base + i * Qn);
+                const int idx = (Qn % 16 == 0) ? pb + i * Qn + (Qn / 16) * PADM * i : padk(base + i * Qn);
 #pragma unroll
                 for (int a = 0; a < NA; ++a) sm[(a * Sh::SMEM + idx) * CST] = v[a * E + beta * Rn + i];
             }
@@ -351,10 +359,10 @@ __device__ __forceinline__ void fft_exchange(T* v, T* sm, int tau) {
 #pragma unroll
         for (int beta = 0; beta < E / R; ++beta) {
             const int nu = tau + Sh::T * beta;
-            const int pn = padidx(nu);
+            const int pn = padk(nu);
 #pragma unroll
             for (int k1 = 0; k1 < R; ++k1) {
-                const int idx = (V % 16 == 0) ? pn + V * k1 + (V / 16) * k1 : padidx(nu + V * k1);
+                const int idx = (V % 16 == 0) ? pn + V * k1 + (V / 16) * PADM * k1 : padk(nu + V * k1);
 #pragma unroll
                 for (int a = 0; a < NA; ++a) v[a * E + beta * R + k1] = sm[(a * Sh::SMEM + idx) * CST];
             }

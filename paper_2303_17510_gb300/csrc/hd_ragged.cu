@@ -180,7 +180,7 @@ int ilog2_exact(int64_t x) {
 size_t fused_group_elems(int64_t S, int A, int aux) {
     const int64_t E = ragged_E((int)S);
     (void)E;
-    return (size_t)A * ((size_t)aux + (size_t)(S + S / 16));
+    return (size_t)A * ((size_t)aux + (size_t)(S + (ragged_E((int)S) == 8 ? S / 8 : S / 16)));   // FftShape::SMEM
 }
 
 size_t fused_tile_smem(int64_t S, int A, int aux) {
