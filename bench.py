@@ -36,6 +36,7 @@ import argparse
 import json
 import math
 import os
+import re
 import subprocess
 import sys
 import threading
@@ -322,16 +323,27 @@ def alu(flops_launch, ms_launch, clocks):
             "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES} FP32 lanes x 2 (FMA) x {mhz:.0f} MHz (sampled)"}
 
 
-def source_digest():
-    """SHA-256 over the CUDA sources (csrc/*), so that DRAM counters taken
-    from an older build of a kernel are not reported for a newer one."""
+_CODE_TOKENS = re.compile(r'("(?:\\.|[^"\\\n])*")|//[^\n]*|/\*.*?\*/', re.S)
+
+
+def code_only(text):
+    """C/C++/CUDA source without its comments, trailing blanks and empty
+    lines (string literals kept)."""
+    text = _CODE_TOKENS.sub(lambda m: m.group(1) or "", text)
+    return "\n".join(ln.rstrip() for ln in text.splitlines() if ln.strip())
+
+
+def source_digest(d=None):
+    """SHA-256 over the code of the CUDA sources (csrc/*, comments left out),
+    so that DRAM counters taken from an older build of a kernel are not
+    reported for a newer one."""
     import hashlib
-    d = os.path.join(ROOT, "paper_2303_17510_gb300", "csrc")
+    d = d or os.path.join(ROOT, "paper_2303_17510_gb300", "csrc")
     h = hashlib.sha256()
     for name in sorted(os.listdir(d)):
         if name.endswith((".cu", ".cuh", ".h")):
             h.update(name.encode())
-            h.update(open(os.path.join(d, name), "rb").read())
+            h.update(code_only(open(os.path.join(d, name), encoding="utf-8").read()).encode())
     return h.hexdigest()[:16]
 
 

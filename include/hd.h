@@ -75,7 +75,7 @@ typedef struct hd_plan hd_plan;
  * HD_CENTERED otherwise (Section 5, Hermitian data: centered outer axes,
  * Hermitian innermost axis).  m[i] = 0 selects parameters automatically;
  * p[i], q[i] = 0 derive them from m (Eq. pqdef1, Alg. convolve/convolveX,
- * Section 5.1-5.2).  D[i] = 0 selects the residue grouping automatically. */
+ * Section 6.1-6.2).  D[i] = 0 selects the residue grouping automatically. */
 typedef struct {
     int ndim;
     int64_t L[3];
@@ -94,7 +94,7 @@ typedef struct {
 
 /* Derive (p, q, n) from (kind, L, M, m): Eq. pqdef1 with Alg. convolve
  * (complex: p = ceil(L/m); p <= 2: q = n = ceil(M/m); p > 2: n =
- * ceil(M/(p m)), q = n p) or Alg. convolveX with Section 5.2 (centered and
+ * ceil(M/(p m)), q = n p) or Alg. convolveX with Section 6.2 (centered and
  * Hermitian: p = 2 ceil(L/(2m)), n = ceil(2M/(p m)), q = n p / 2).  n is the
  * number of residue contributions.  Host only; no device is needed.
  * Returns HD_ERR_INVALID for non-positive L, M, m or an unknown kind. */
@@ -145,7 +145,7 @@ hd_status hd_plan_get_axis_params(const hd_plan* plan, int axis, int64_t* m, int
 /* Residue contribution r of one stored 1D input (the forward residue
  * transform alone, without mult or the backward transform).  Writes the values of residue r in the order the
  * paper's transforms return them (Section 2.2 forward1/forward2: F_{q l + r},
- * l < m; Section 5.1-5.2 inner: F[u m + l] = F_{q l + u n + v}), i.e. m
+ * l < m; Section 6.1-6.2 inner: F[u m + l] = F_{q l + u n + v}), i.e. m
  * values for complex p <= 2 and centered/Hermitian p = 2, p m values for
  * complex p > 2, p m / 2 for centered/Hermitian p > 2.  For Hermitian
  * plans the values are real and stored with zero imaginary part.  r < n.
@@ -153,7 +153,7 @@ hd_status hd_plan_get_axis_params(const hd_plan* plan, int axis, int64_t* m, int
 hd_status hd_forward_residue(const hd_plan* plan, const void* f, int64_t r, void* out, void* stream);
 
 /* ---------------------------------------------------------------------------
- * Parameter selection (the paper's optimizer, Section 6: scan m, D and the
+ * Parameter selection (the paper's optimizer, Section 7: scan m, D and the
  * transform variant, time each candidate, keep the fastest).
  * ------------------------------------------------------------------------- */
 
@@ -196,7 +196,7 @@ hd_status hd_tune_cache_clear(void);
 
 /* ---------------------------------------------------------------------------
  * Learned parameter selector (not in the paper; it stands in for the timed
- * search of Section 6).  A small MLP predicts the log time of one convolution
+ * search of Section 7).  A small MLP predicts the log time of one convolution
  * for a (problem, candidate) pair; an installed ensemble picks the candidate
  * with the lowest mean prediction.  Training runs on the GPU with the
  * library's own kernels: tanh hidden layers, a linear output, mean squared
@@ -248,7 +248,7 @@ hd_status hd_selector_choose(const hd_desc* d, hd_candidate* out, int* confident
 /* ---------------------------------------------------------------------------
  * Ragged batches: many 1D convolutions of different L, M, A and kind in one
  * persistent kernel launch, replayed from a CUDA graph.  (The paper computes
- * C copies of one transform with multithreading, Section 6; a ragged batch
+ * C copies of one transform with multithreading, Section 7; a ragged batch
  * generalizes the copies to different sizes.)  FP32, complex and centered
  * kinds, A = 2 (product) or 3 (sum of pairwise products), B = 1.
  * ------------------------------------------------------------------------- */

@@ -13,16 +13,16 @@ Modules
               Hermitian; 1D and separable N-D; sampled output points).  Exact on
               integer-valued inputs.  Section 2 (problem statement), Sections 3-5.
   params   -- parameter derivation p, q, n of Alg. convolve / convolveX and the
-              inner-loop redefinition (Eq. pqdef1, Section 5.1, Section 5.2);
+              inner-loop redefinition (Eq. pqdef1, Section 6.1, Section 6.2);
               dealiasing bounds; work-memory formulas (Section 4/5, memory).
   residue  -- per-residue forward transforms by their definition: the length-qm
               DFT of the zero-padded (or centered) input at k = q*l + r
-              (Eq. forStan, Eq. centDFT, Eq. wHerDef, Section 5.1-5.2).
+              (Eq. forStan, Eq. centDFT, Eq. wHerDef, Section 6.1-6.2).
   steps    -- the paper's residue-at-a-time algorithm (Alg. convolve/convolveX
               with forward1/2/Inner, centered and Hermitian variants) in the
               paper's order, with an FFT library call as the size-m FFT step.
   explicit -- explicit zero-padded FFT convolution (the paper's comparison
-              method, Section 6) with numpy's FFT as the FFT step.
+              method, Section 7) with numpy's FFT as the FFT step.
   cdirect  -- ctypes wrapper of direct_conv.c, the same definition in plain C
               (multithreaded over instances) for large samples and CPU timing.
   mlp      -- FP64 reference of the parameter-selector MLP (forward, backward,

@@ -4,7 +4,7 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
 Explicit dealiasing pads every input with zeros to a length N >= M, takes
 length-N FFTs, applies ``mult`` pointwise and inverse transforms (Section 1,
-Section 6).  numpy's FFT is the FFT step.  For centered data the zero
+Section 7).  numpy's FFT is the FFT step.  For centered data the zero
 padding is applied symmetrically by transforming at the centered offsets;
 for Hermitian data the expanded symmetric array is used.  Used as the
 full-field oracle of the multidimensional workloads, where the direct sum is

@@ -4,14 +4,14 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
 Given the FFT size m, the paper derives the explicit padding factor p and the
 implicit padding factor q (Eq. pqdef1, Section 2.1), then, per Alg. convolve
-(Section 2.2) and the inner-loop redefinition (Section 5.1):
+(Section 2.2) and the inner-loop redefinition (Section 6.1):
     p = ceil(L/m);   p <= 2: n = q = ceil(M/m)
                      p  > 2: n = ceil(M/(p m)), q = n p
-and per Alg. convolveX (Section 3/4) with Section 5.2 for centered and
+and per Alg. convolveX (Section 3/4) with Section 6.2 for centered and
 Hermitian data:
     p = 2 ceil(L/(2m)) (even);  n = ceil(2M/(p m)),  q = n p / 2.
 n is the number of residue contributions the convolution loop visits.  An
-explicit plan (m >= M, p = q = n = 1) is legal for every kind (Section 6, the
+explicit plan (m >= M, p = q = n = 1) is legal for every kind (Section 7, the
 optimizer example at L = 2048).
 """
 from __future__ import annotations

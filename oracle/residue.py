@@ -12,7 +12,7 @@ Residue contributions, in the order the paper's transforms return them:
   p <= 2 (complex) or p = 2 (centered/Hermitian): residue r < q returns
        F_r[l] = F_{q l + r},            l < m          (Eq. forStan, Eq. forCent)
   p  > 2 (complex):  residue v < n returns
-       F_v[u m + l] = F_{q l + u n + v},  u < p,  l < m  (Section 5.1)
+       F_v[u m + l] = F_{q l + u n + v},  u < p,  l < m  (Section 6.1)
   p  > 2 (centered/Hermitian): residue v < n returns
        F_v[u m + l] = F_{q l + u n + v},  u < p/2, l < m (Eq. forCentIn)
 """

@@ -13,13 +13,13 @@ equations in the paper's order:
                                    backward2 uses zeta_qm^{-s r} for s >= m
                                    (Eq. invStan with t = 1; the printed
                                    exponent -(s-m) r drops zeta_q^{-r})
-  forwardInner / backwardInner (p > 2)   Section 5.1: twist zeta_q^{vt}, size-p
+  forwardInner / backwardInner (p > 2)   Section 6.1: twist zeta_q^{vt}, size-p
                                    DFTs along t, twiddle zeta_qm^{(un+v)s},
                                    size-m FFTs; Eq. invInner backwards
   forward2C / backward2C (p = 2)   Eq. wDef with out-of-range f taken as 0;
                                    backward stores zeta_qm^{-r c} W_{c mod m} at
                                    each centered output c (Eq. invStan, Section 3)
-  forwardInnerC / backwardInnerC   Section 5.2 (fold factor zeta_n^{-v})
+  forwardInnerC / backwardInnerC   Section 6.2 (fold factor zeta_n^{-v})
   forward2H / backward2H,          as the centered transforms with
   forwardInnerH / backwardInnerH   f_{-j} = conj f_j (Eq. wHerDef); the size-m
                                    transforms are complex-to-real forward

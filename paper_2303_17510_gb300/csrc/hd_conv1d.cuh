@@ -17,9 +17,9 @@
 //                                 Eq. forStan with t = 0, 1)
 //   complex p  > 2  (S = p m):   i = j (S >= L)          (forwardInner; the size-p
 //                                 DFTs along t and the size-m FFTs form one
-//                                 size-pm FFT, Section 5.1)
+//                                 size-pm FFT, Section 6.1)
 //   centered        (S = p m/2): i in {j, j - S}         (forward2C, Eq. wDef;
-//                                 forwardInnerC, Section 5.2, fold factor
+//                                 forwardInnerC, Section 6.2, fold factor
 //                                 zeta_n^{-v} = zeta_N^{-v S})
 //   Hermitian       (S = p m/2): as centered with f_{-c} = conj f_c (Eq. wHerDef)
 // and the backward contribution of residue r to h_i is

@@ -5,7 +5,7 @@
 // butterflies in registers (a final smaller radix when log2 S is not a
 // multiple of log2 E), and between passes the group exchanges values through
 // shared memory.  This is the size-m FFT of the method (Section 2: the
-// unpadded FFTs the residue transforms call; Section 5.1: for p > 2 the
+// unpadded FFTs the residue transforms call; Section 6.1: for p > 2 the
 // size-p DFTs along t and the size-m FFTs along s form one size-pm FFT).
 //
 // Sign convention (Section 2): the forward transform is

@@ -3,7 +3,7 @@
 // kernels, and the selector that uses an ensemble of such networks to pick a
 // candidate (m, p, q, D, kernel variant) without timing, falling back to the
 // timed search when the ensemble is unsure.  The paper has no selector; its
-// optimizer (Section 6) is the timed search this stands in for.
+// optimizer (Section 7) is the timed search this stands in for.
 //
 // Network: h_0 = x; z_l = h_l W_l^T + b_l; h_{l+1} = tanh(z_l) for hidden
 // layers; the last layer is linear with one output, the predicted log time of

@@ -45,7 +45,7 @@ int64_t next_pow2(int64_t x) {
 }
 
 // (p, q) from m for an axis when the caller leaves them at 0 (Eq. pqdef1,
-// Alg. convolve / convolveX, Section 5.1-5.2); p given, q derived likewise.
+// Alg. convolve / convolveX, Section 6.1-6.2); p given, q derived likewise.
 void derive_pq(int kind, int64_t L, int64_t M, int64_t m, int64_t* p, int64_t* q) {
     int64_t pp = *p, qq = *q, nn;
     if (pp == 0) {

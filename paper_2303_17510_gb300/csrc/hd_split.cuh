@@ -1,7 +1,7 @@
 // hd_split.cuh -- residue transforms larger than one CTA (the "split" path).
 //
 // A residue transform of size S = S1 * S2 (S2 <= the fused limit, S1 <= 16)
-// is computed in the order of the paper's inner loop (Section 5.1,
+// is computed in the order of the paper's inner loop (Section 6.1,
 // forwardInner / backwardInner): size-S1 DFTs along the block index t (here
 // j1), the twiddle zeta_S^{j2 k1}, then size-S2 FFTs along s (here j2):
 //     X_{k1 + S1 k2} = sum_{j2} zeta_{S2}^{j2 k2} zeta_S^{j2 k1}

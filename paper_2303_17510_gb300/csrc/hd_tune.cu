@@ -1,5 +1,5 @@
 // hd_tune.cu -- candidate enumeration, device-timed autotuning and the
-// process-wide tuning cache (the paper's empirical optimizer, Section 6:
+// process-wide tuning cache (the paper's empirical optimizer, Section 7:
 // scan the FFT size m and the residue blocking, time, keep the fastest).
 #include <cuda_runtime.h>
 

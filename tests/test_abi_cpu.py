@@ -48,7 +48,7 @@ def test_derive_params_matches_oracle(hd, kind):
 
 def test_paper_examples_through_abi(hd):
     assert hd.derive_params("complex", 6, 11, 4)[:2] == (2, 3)             # Fig. 1
-    assert hd.derive_params("centered", 2048, 3072, 16)[:2] == (128, 192)  # Section 6.2 example
+    assert hd.derive_params("centered", 2048, 3072, 16)[:2] == (128, 192)  # Section 7.2 example
 
 
 @pytest.mark.parametrize("kind", ["complex", "centered", "hermitian"])

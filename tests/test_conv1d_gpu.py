@@ -99,7 +99,7 @@ def test_auto_parameters(hd, kind, dtype):
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
 def test_forward_residue_intermediates(hd, kind, dtype):
     """Each residue contribution equals the naive length-qm DFT at k = q l + r
-    (Eq. forStan), k = q l + u n + v (Section 5.1) or the centered/Hermitian
+    (Eq. forStan), k = q l + u n + v (Section 6.1) or the centered/Hermitian
     analogues (Eq. centDFT, Eq. forCentIn)."""
     import torch
     L = 37

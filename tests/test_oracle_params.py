@@ -29,7 +29,7 @@ def test_paper_examples(row):
 
 
 def test_explicit_plan_example():
-    # Section 6.2: y direction explicit m = 3072, p = q = 1 for M = 3072
+    # Section 7.2: y direction explicit m = 3072, p = q = 1 for M = 3072
     assert params.explicit(2048, 3072, 3072) == (1, 1, 1)
     with pytest.raises(ValueError):
         params.explicit(2048, 3072, 2048)

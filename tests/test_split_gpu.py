@@ -1,6 +1,6 @@
 """GPU parity of the split path (residue transforms larger than one CTA,
 computed as size-S1 DFTs along the block index and size-S2 row FFTs through a
-work buffer, Section 5.1) against the FP64 direct oracle."""
+work buffer, Section 6.1) against the FP64 direct oracle."""
 import numpy as np
 import pytest
 
