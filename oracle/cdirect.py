@@ -11,6 +11,8 @@ import subprocess
 
 import numpy as np
 
+from . import direct
+
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "direct_conv.c")
 _OUT = os.path.join(_HERE, "_build", "liboracle_direct.so")
@@ -49,8 +51,19 @@ def _load():
     return _lib
 
 
+def _multi(fn, fs, mult, *args):
+    """B > 1 outputs (the Basdevant forms): each output is a signed sum of
+    binary product convolutions, computed by the C product one pair at a time."""
+    A, terms = direct.MULT_TERMS[mult]
+    assert len(fs) == A
+    return np.stack([sum(c * fn([fs[i], fs[j]], *args) for i, j, c in t) for t in terms])
+
+
 def conv1d_batch(fs, L: int, kind="complex", mult="product", nthreads=None) -> np.ndarray:
-    """fs: list of A arrays of shape (count, n) -> (count, n) complex128 output."""
+    """fs: list of A arrays of shape (count, n) -> (count, n) complex128 output,
+    or (B, count, n) for a mult with B > 1 outputs."""
+    if mult not in MULT:
+        return _multi(lambda g: conv1d_batch(g, L, kind, "product", nthreads), fs, mult)
     lib = _load()
     fs = [np.ascontiguousarray(f, dtype=np.complex128) for f in fs]
     count = fs[0].shape[0]
@@ -64,6 +77,8 @@ def conv1d_batch(fs, L: int, kind="complex", mult="product", nthreads=None) -> n
 
 
 def conv1d_points(fs, L: int, idx, kind="complex", mult="product") -> np.ndarray:
+    if mult not in MULT:
+        return _multi(lambda g: conv1d_points(g, L, idx, kind, "product"), fs, mult)
     lib = _load()
     fs = [np.ascontiguousarray(f, dtype=np.complex128) for f in fs]
     idx = np.ascontiguousarray(idx, dtype=np.int64)

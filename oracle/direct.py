@@ -18,9 +18,17 @@ depend on m, p or q, so the oracle is the direct sum, written out:
                            2*ceil(L/2)-1) array is convolved as centered and
                            the non-negative half is returned.  Im f_0 is ignored.
 
-Multiplication operators (``mult``):
+Multiplication operators (``mult``); output b is a signed sum of pairwise
+convolutions f_i*f_j, since a pointwise product of DFTs is the DFT of a
+convolution:
   "product"     A=2, B=1:  F1*F2                    -> f1*f2
   "sum_pairs3"  A=3, B=1:  F1F2 + F2F3 + F3F1       -> f1*f2 + f2*f3 + f3*f1
+  "basdevant2"  A=2, B=2:  (F1F2, F1^2 - F2^2)      -> (f1*f2, f1*f1 - f2*f2)
+  "basdevant3"  A=3, B=5:  (F1F2, F2F3, F3F1, F1^2 - F3^2, F2^2 - F3^2)
+The Basdevant products are the nonlinear terms of incompressible
+Navier-Stokes in Basdevant's form, which Section 9 counts as A = B = 2 in two
+dimensions and A = 3, B = 5 in three (inputs: the velocity components).  With
+B > 1 the functions below return the B outputs stacked on a new first axis.
 On integer-valued inputs every product and partial sum is an integer below
 2^53, so these FP64 sums are exact.
 """
@@ -31,7 +39,15 @@ import itertools
 import numpy as np
 
 KINDS = ("complex", "centered", "hermitian")
-MULTS = {"product": 2, "sum_pairs3": 3}
+# mult -> (A, terms): output b = sum of c * (f_i * f_j) over (i, j, c) in terms[b]
+MULT_TERMS = {
+    "product": (2, [[(0, 1, 1)]]),
+    "sum_pairs3": (3, [[(0, 1, 1), (1, 2, 1), (2, 0, 1)]]),
+    "basdevant2": (2, [[(0, 1, 1)], [(0, 0, 1), (1, 1, -1)]]),
+    "basdevant3": (3, [[(0, 1, 1)], [(1, 2, 1)], [(2, 0, 1)], [(0, 0, 1), (2, 2, -1)], [(1, 1, 1), (2, 2, -1)]]),
+}
+MULTS = {k: v[0] for k, v in MULT_TERMS.items()}             # inputs A
+OUTPUTS = {k: len(v[1]) for k, v in MULT_TERMS.items()}      # outputs B
 
 
 def full_linear(a: np.ndarray, b: np.ndarray) -> np.ndarray:
@@ -52,39 +68,42 @@ def hermitian_expand(f: np.ndarray) -> np.ndarray:
     return np.concatenate([np.conj(f[:0:-1]), f])
 
 
-def _pairs(fs, mult):
-    if mult == "product":
-        assert len(fs) == 2
-        return [(0, 1)]
-    if mult == "sum_pairs3":
-        assert len(fs) == 3
-        return [(0, 1), (1, 2), (2, 0)]
-    raise ValueError(mult)
+def _outputs(fs, mult, conv):
+    """The B outputs of ``mult``: signed sums of conv(f_i, f_j), stacked when B > 1."""
+    if mult not in MULT_TERMS:
+        raise ValueError(mult)
+    A, terms = MULT_TERMS[mult]
+    assert len(fs) == A
+    outs = [sum(c * conv(fs[i], fs[j]) for i, j, c in t) for t in terms]
+    return outs[0] if len(outs) == 1 else np.stack(outs)
 
 
 def conv1d(fs, kind: str = "complex", mult: str = "product") -> np.ndarray:
-    """One 1D convolution of the A stored inputs ``fs``; returns the stored output."""
+    """One 1D convolution of the A stored inputs ``fs``; returns the stored
+    output (shape (B, ...) when B > 1)."""
     fs = [np.asarray(f, dtype=np.complex128) for f in fs]
     if kind == "hermitian":
         H = fs[0].shape[-1]
         ex = [hermitian_expand(f) for f in fs]
-        full = sum(full_linear(ex[i], ex[j]) for i, j in _pairs(ex, mult))
+        full = _outputs(ex, mult, full_linear)
         # expanded length Le = 2H-1, centered offset H-1; full index k <-> c = k - 2(H-1)
-        return full[2 * (H - 1): 2 * (H - 1) + H]
+        return full[..., 2 * (H - 1): 2 * (H - 1) + H]
     L = fs[0].shape[-1]
-    full = sum(full_linear(fs[i], fs[j]) for i, j in _pairs(fs, mult))
+    full = _outputs(fs, mult, full_linear)
     if kind == "complex":
-        return full[:L]
+        return full[..., :L]
     if kind == "centered":
         Hc = L // 2
-        return full[Hc:Hc + L]
+        return full[..., Hc:Hc + L]
     raise ValueError(kind)
 
 
 def conv1d_batch(fs, kind="complex", mult="product") -> np.ndarray:
-    """Row-wise conv1d over a batch: fs is a list of A arrays of shape (count, L)."""
+    """Row-wise conv1d over a batch: fs is a list of A arrays of shape (count, L);
+    returns (count, L), or (B, count, L) when B > 1."""
     count = fs[0].shape[0]
-    return np.stack([conv1d([f[b] for f in fs], kind, mult) for b in range(count)])
+    out = np.stack([conv1d([f[b] for f in fs], kind, mult) for b in range(count)])
+    return out if OUTPUTS[mult] == 1 else np.moveaxis(out, 1, 0)
 
 
 # ---------------------------------------------------------------------------
@@ -144,15 +163,15 @@ def convnd(fs, kinds, mult="product") -> np.ndarray:
     if kinds[-1] == "hermitian":
         H = fs[0].shape[-1]
         ex = [hermitian_expand_nd(f, f.shape[:-1]) for f in fs]
-        full = sum(_full_linear_nd(ex[i], ex[j]) for i, j in _pairs(ex, mult))
-        sl = []
+        full = _outputs(ex, mult, _full_linear_nd)
+        sl = [Ellipsis]
         for ax, k in enumerate(kinds[:-1]):
             L = fs[0].shape[ax]
             sl.append(slice(L // 2, L // 2 + L) if k == "centered" else slice(0, L))
         sl.append(slice(2 * (H - 1), 2 * (H - 1) + H))
         return full[tuple(sl)]
-    full = sum(_full_linear_nd(fs[i], fs[j]) for i, j in _pairs(fs, mult))
-    sl = []
+    full = _outputs(fs, mult, _full_linear_nd)
+    sl = [Ellipsis]
     for ax, k in enumerate(kinds):
         L = fs[0].shape[ax]
         sl.append(slice(L // 2, L // 2 + L) if k == "centered" else slice(0, L))
@@ -179,7 +198,9 @@ def convnd_points(fs, kinds, points, mult="product") -> np.ndarray:
         lo = [-(fs[0].shape[a] // 2) if kinds[a] == "centered" else 0 for a in range(nd)]
         out_lo = lo
     shape = ex[0].shape
-    res = np.zeros(len(points), dtype=np.complex128)
+    A, terms = MULT_TERMS[mult]
+    assert len(ex) == A
+    res = np.zeros((len(terms), len(points)), dtype=np.complex128)
     for pi, pt in enumerate(np.asarray(points)):
         c = [int(pt[a]) + out_lo[a] for a in range(nd)]       # centered output index
         # c' ranges over the stored range of axis a: lo_a .. lo_a + n_a - 1
@@ -198,11 +219,9 @@ def convnd_points(fs, kinds, points, mult="product") -> np.ndarray:
             sl_b.append(slice(c[a] - c1 - lo[a], c[a] - c2 - lo[a] - 1 if c[a] - c2 - lo[a] - 1 >= 0 else None, -1))
         if empty:
             continue
-        tot = 0j
-        for i, j in _pairs(ex, mult):
-            tot += np.sum(ex[i][tuple(sl_a)] * ex[j][tuple(sl_b)])
-        res[pi] = tot
-    return res
+        for b, t in enumerate(terms):
+            res[b, pi] = sum(c * np.sum(ex[i][tuple(sl_a)] * ex[j][tuple(sl_b)]) for i, j, c in t)
+    return res[0] if len(terms) == 1 else res
 
 
 def conv1d_points(fs, kind, points, mult="product") -> np.ndarray:

@@ -14,11 +14,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .direct import hermitian_expand_nd
-
-
-def _pairs(n, mult):
-    return [(0, 1)] if mult == "product" else [(0, 1), (1, 2), (2, 0)]
+from .direct import MULT_TERMS, hermitian_expand_nd
 
 
 def convnd_explicit(fs, kinds, Ns, mult="product") -> np.ndarray:
@@ -40,9 +36,13 @@ def convnd_explicit(fs, kinds, Ns, mult="product") -> np.ndarray:
         idx = np.ix_(*[np.mod(np.arange(e.shape[a]) + lo[a], Ns[a]) for a in axes])
         P[idx] = e
         padded.append(np.fft.fftn(P, axes=axes))
-    spec = sum(padded[i] * padded[j] for i, j in _pairs(len(padded), mult))
-    full = np.fft.ifftn(spec, axes=axes)
+    A, terms = MULT_TERMS[mult]
+    assert len(padded) == A
     out_lo = lo[:-1] + [0] if herm else lo
     out_shape = fs[0].shape
     idx = np.ix_(*[np.mod(np.arange(out_shape[a]) + out_lo[a], Ns[a]) for a in axes])
-    return full[idx]
+    outs = []
+    for t in terms:   # mult, pointwise on the padded spectra
+        spec = sum(c * padded[i] * padded[j] for i, j, c in t)
+        outs.append(np.fft.ifftn(spec, axes=axes)[idx])
+    return outs[0] if len(outs) == 1 else np.stack(outs)

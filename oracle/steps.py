@@ -249,11 +249,31 @@ def backwardInnerH(F, L, m, p, q, n, v):
 # ------------------------------------------------------------------ drivers
 
 def _mult(Fs, mult):
+    """The B transformed outputs of one residue, pointwise in the A transformed
+    inputs (the Basdevant forms of Section 9: velocity components in, the
+    products of the nonlinear term out)."""
     if mult == "product":
-        return Fs[0] * Fs[1]
+        return [Fs[0] * Fs[1]]
     if mult == "sum_pairs3":
-        return Fs[0] * Fs[1] + Fs[1] * Fs[2] + Fs[2] * Fs[0]
+        return [Fs[0] * Fs[1] + Fs[1] * Fs[2] + Fs[2] * Fs[0]]
+    if mult == "basdevant2":
+        u, v = Fs
+        return [u * v, u * u - v * v]
+    if mult == "basdevant3":
+        u, v, w = Fs
+        return [u * v, v * w, w * u, u * u - w * w, v * v - w * w]
     raise ValueError(mult)
+
+
+def _accumulate(h, Hs, backward):
+    """h_b += backward(H_b) for each output b (Alg. convolve: every output
+    accumulates its residue contribution)."""
+    for b, Hb in enumerate(Hs):
+        h[b] += backward(Hb)
+
+
+def _outputs(h):
+    return h[0] if h.shape[0] == 1 else h
 
 
 def convolve(fs, L, M, m, mult="product", p=None, q=None):
@@ -263,18 +283,22 @@ def convolve(fs, L, M, m, mult="product", p=None, q=None):
     else:
         n = q if p <= 2 else q // p
     fs = [np.asarray(f, dtype=np.complex128) for f in fs]
-    h = np.zeros(L, dtype=np.complex128)
+    h = None
     for r in range(n):
         if p == 1:
             Fs = [forward1(f, L, m, q, r) for f in fs]
-            h += backward1(_mult(Fs, mult), L, m, q, r)
+            back = lambda F: backward1(F, L, m, q, r)
         elif p == 2:
             Fs = [forward2(f, L, m, q, r) for f in fs]
-            h += backward2(_mult(Fs, mult), L, m, q, r)
+            back = lambda F: backward2(F, L, m, q, r)
         else:
             Fs = [forwardInner(f, L, m, p, q, n, r) for f in fs]
-            h += backwardInner(_mult(Fs, mult), L, m, p, q, n, r)
-    return h / (q * m)
+            back = lambda F: backwardInner(F, L, m, p, q, n, r)
+        Hs = _mult(Fs, mult)
+        if h is None:
+            h = np.zeros((len(Hs), L), dtype=np.complex128)
+        _accumulate(h, Hs, back)
+    return _outputs(h) / (q * m)
 
 
 def convolveX(fs, L, M, m, kind="centered", mult="product"):
@@ -282,24 +306,32 @@ def convolveX(fs, L, M, m, kind="centered", mult="product"):
     p, q, n = derive(kind, L, M, m)
     fs = [np.asarray(f, dtype=np.complex128) for f in fs]
     if kind == "centered":
-        h = np.zeros(L, dtype=np.complex128)
+        h = None
         for r in range(n):
             if p == 2:
                 Fs = [forward2C(f, L, m, q, r) for f in fs]
-                h += backward2C(_mult(Fs, mult), L, m, q, r)
+                back = lambda F: backward2C(F, L, m, q, r)
             else:
                 Fs = [forwardInnerC(f, L, m, p, q, n, r) for f in fs]
-                h += backwardInnerC(_mult(Fs, mult), L, m, p, q, n, r)
-        return h / (q * m)
+                back = lambda F: backwardInnerC(F, L, m, p, q, n, r)
+            Hs = _mult(Fs, mult)
+            if h is None:
+                h = np.zeros((len(Hs), L), dtype=np.complex128)
+            _accumulate(h, Hs, back)
+        return _outputs(h) / (q * m)
     if kind == "hermitian":
         Hc = (L + 1) // 2
-        h = np.zeros(Hc, dtype=np.complex128)
+        h = None
         for r in range(n):
             if p == 2:
                 Fs = [forward2H(f, L, m, q, r) for f in fs]
-                h += backward2H(_mult(Fs, mult), L, m, q, r)
+                back = lambda F: backward2H(F, L, m, q, r)
             else:
                 Fs = [forwardInnerH(f, L, m, p, q, n, r) for f in fs]
-                h += backwardInnerH(_mult(Fs, mult), L, m, p, q, n, r)
-        return h / (q * m)
+                back = lambda F: backwardInnerH(F, L, m, p, q, n, r)
+            Hs = _mult(Fs, mult)
+            if h is None:
+                h = np.zeros((len(Hs), Hc), dtype=np.complex128)
+            _accumulate(h, Hs, back)
+        return _outputs(h) / (q * m)
     raise ValueError(kind)

@@ -32,12 +32,30 @@ def brute_1d(fs, kind, mult):
             d[-c] = f[c].conjugate()
         return d
     ds = [as_dict(f) for f in fs]
-    pairs = [(0, 1)] if mult == "product" else [(0, 1), (1, 2), (2, 0)]
-    out = {}
-    for a, b in pairs:
+
+    def conv(a, b):
+        out = {}
         for i, x in ds[a].items():
             for k, y in ds[b].items():
                 out[i + k] = out.get(i + k, 0) + x * y
+        return out
+
+    def lin(*terms):   # sum of c * dict
+        out = {}
+        for c, d in terms:
+            for k, v in d.items():
+                out[k] = out.get(k, 0) + c * v
+        return out
+
+    if mult == "product":
+        outs = [conv(0, 1)]
+    elif mult == "sum_pairs3":
+        outs = [lin((1, conv(0, 1)), (1, conv(1, 2)), (1, conv(2, 0)))]
+    elif mult == "basdevant2":        # u v, u^2 - v^2
+        outs = [conv(0, 1), lin((1, conv(0, 0)), (-1, conv(1, 1)))]
+    else:                             # u v, v w, w u, u^2 - w^2, v^2 - w^2
+        outs = [conv(0, 1), conv(1, 2), conv(2, 0), lin((1, conv(0, 0)), (-1, conv(2, 2))),
+                lin((1, conv(1, 1)), (-1, conv(2, 2)))]
     n = len(fs[0])
     if kind == "complex":
         keys = range(n)
@@ -45,13 +63,17 @@ def brute_1d(fs, kind, mult):
         keys = range(-(n // 2), n - n // 2)
     else:
         keys = range(n)
-    return np.array([out.get(k, 0) for k in keys], dtype=np.complex128)
+    res = np.array([[o.get(k, 0) for k in keys] for o in outs], dtype=np.complex128)
+    return res[0] if len(outs) == 1 else res
+
+
+ALL_MULTS = ["product", "sum_pairs3", "basdevant2", "basdevant3"]
 
 
 @pytest.mark.parametrize("kind", ["complex", "centered", "hermitian"])
-@pytest.mark.parametrize("mult", ["product", "sum_pairs3"])
+@pytest.mark.parametrize("mult", ALL_MULTS)
 def test_brute_force_tiny(kind, mult):
-    A = 2 if mult == "product" else 3
+    A = direct.MULTS[mult]
     for L in range(1, 13):
         if kind == "hermitian":
             fs = [inputs.hermitian_1d(1, L, 100 + L + a, integer=True)[0] for a in range(A)]
@@ -133,9 +155,9 @@ def test_hermitian_matches_centered_on_expanded():
 
 
 @pytest.mark.parametrize("kind", ["complex", "centered", "hermitian"])
-@pytest.mark.parametrize("mult", ["product", "sum_pairs3"])
+@pytest.mark.parametrize("mult", ALL_MULTS)
 def test_c_oracle_equals_numpy(kind, mult):
-    A = 2 if mult == "product" else 3
+    A = direct.MULTS[mult]
     for L in (1, 2, 7, 64, 129):
         if kind == "hermitian":
             fs = [inputs.hermitian_1d(3, L, 11 + a, integer=True) for a in range(A)]
@@ -146,9 +168,9 @@ def test_c_oracle_equals_numpy(kind, mult):
         assert np.array_equal(got, ref), (kind, mult, L)
         idx = np.arange(fs[0].shape[1])[::3]
         pts = cdirect.conv1d_points([f[0] for f in fs], L, idx, kind, mult)
-        assert np.array_equal(pts, ref[0, idx])
+        assert np.array_equal(pts, ref[..., 0, idx])
         pts2 = direct.conv1d_points([f[0] for f in fs], kind, idx, mult)
-        assert np.array_equal(pts2, ref[0, idx])
+        assert np.array_equal(pts2, ref[..., 0, idx])
 
 
 def test_integer_exactness_large():
@@ -244,3 +266,68 @@ def test_explicit_fft_equals_direct(kinds):
     ref = direct.convnd([f, g], kinds)
     got = explicit.convnd_explicit([f, g], kinds, Ns)
     assert np.allclose(got, ref, atol=1e-11)
+
+
+@pytest.mark.parametrize("kind", ["complex", "centered", "hermitian"])
+def test_basdevant_special_cases(kind):
+    """Basdevant outputs against the binary product: u v is the product
+    convolution; with v = 0 the second output is u*u; with u = v it vanishes;
+    swapping u and v keeps u v and negates u^2 - v^2."""
+    L = 19
+    if kind == "hermitian":
+        u, v, w = inputs.hermitian_1d(3, L, 71)
+    else:
+        u, v, w = inputs.uniform_complex((3, L), 71)
+    b = direct.conv1d([u, v], kind, "basdevant2")
+    assert b.shape == (2, len(u))
+    assert np.allclose(b[0], direct.conv1d([u, v], kind), atol=1e-13)
+    z = np.zeros_like(v)
+    b0 = direct.conv1d([u, z], kind, "basdevant2")
+    assert np.allclose(b0[1], direct.conv1d([u, u], kind), atol=1e-13) and not np.any(b0[0])
+    assert np.allclose(direct.conv1d([u, u], kind, "basdevant2")[1], 0, atol=1e-13)
+    bs = direct.conv1d([v, u], kind, "basdevant2")
+    assert np.allclose(bs[0], b[0], atol=1e-13) and np.allclose(bs[1], -b[1], atol=1e-13)
+    # 3D form: with w = 0 it holds the 2D form's outputs (and zeros)
+    b3 = direct.conv1d([u, v, np.zeros_like(w)], kind, "basdevant3")
+    assert b3.shape == (5, len(u))
+    assert np.allclose(b3[0], b[0], atol=1e-13) and not np.any(b3[1]) and not np.any(b3[2])
+    assert np.allclose(b3[3] - b3[4], b[1], atol=1e-13)
+
+
+@pytest.mark.parametrize("mult", ["basdevant2", "basdevant3"])
+def test_multi_output_batch_points_and_nd(mult):
+    """B > 1: the batch, point and N-D forms agree with the 1D definition and
+    the explicit FFT convolution, output by output."""
+    A, B = direct.MULTS[mult], direct.OUTPUTS[mult]
+    fs = [inputs.integer_complex((3, 9), 81 + a) for a in range(A)]
+    for kind in ("complex", "centered"):
+        ref = direct.conv1d_batch(fs, kind, mult)
+        assert ref.shape == (B, 3, 9)
+        for i in range(3):
+            assert np.array_equal(ref[:, i], brute_1d([f[i] for f in fs], kind, mult))
+        idx = np.array([0, 4, 8])
+        pts = direct.conv1d_points([f[1] for f in fs], kind, idx, mult)
+        assert np.array_equal(pts, ref[:, 1, idx])
+    f2 = [inputs.uniform_complex((5, 4), 91 + a) for a in range(A)]
+    kinds = ("centered", "complex")
+    h = direct.convnd(f2, kinds, mult)
+    assert h.shape == (B, 5, 4)
+    got = explicit.convnd_explicit(f2, kinds, [8, 7], mult)
+    assert np.allclose(got, h, atol=1e-12)
+    pts = np.array([[0, 0], [2, 3], [4, 1]])
+    assert np.allclose(direct.convnd_points(f2, kinds, pts, mult), h[(slice(None),) + tuple(pts.T)], atol=1e-12)
+    f3 = [inputs.hermitian_3d(6, 95 + a).astype(np.complex128) for a in range(A)]
+    k3 = ("centered", "centered", "hermitian")
+    h3 = direct.convnd(f3, k3, mult)
+    assert np.allclose(explicit.convnd_explicit(f3, k3, [9, 9, 9], mult), h3, atol=1e-11)
+
+
+def test_basdevant_planted_sign_fails(monkeypatch):
+    """A slip in the Basdevant terms (u^2 + v^2 for u^2 - v^2) breaks the
+    brute-force pin."""
+    fs = [inputs.integer_complex(7, 97 + a) for a in range(2)]
+    ok = direct.conv1d(fs, "centered", "basdevant2")
+    assert np.array_equal(ok, brute_1d(fs, "centered", "basdevant2"))
+    monkeypatch.setitem(direct.MULT_TERMS, "basdevant2", (2, [[(0, 1, 1)], [(0, 0, 1), (1, 1, 1)]]))
+    bad = direct.conv1d(fs, "centered", "basdevant2")
+    assert not np.array_equal(bad, brute_1d(fs, "centered", "basdevant2"))

@@ -54,6 +54,22 @@ def test_steps_sum_pairs3(kind):
 
 
 @pytest.mark.parametrize("kind", ["complex", "centered", "hermitian"])
+@pytest.mark.parametrize("mult", ["basdevant2", "basdevant3"])
+def test_steps_multi_output(kind, mult):
+    """B > 1 outputs: each accumulates its own residue contributions; the
+    algorithm equals the definition for every m."""
+    A = 2 if mult == "basdevant2" else 3
+    for L in (4, 7):
+        fs = _fs(kind, L, 88, A=A)
+        ref = direct.conv1d(fs, kind, mult)
+        M = params.dealias_bound(kind, L, mult)
+        for m in range(1, M + 2):
+            got = _run_steps(kind, fs, L, M, m, mult)
+            assert got.shape == ref.shape
+            assert np.allclose(got, ref, atol=1e-11), (kind, mult, L, m)
+
+
+@pytest.mark.parametrize("kind", ["complex", "centered", "hermitian"])
 def test_explicit_at_qm_equals_definition(kind):
     for L in range(1, 11):
         fs = _fs(kind, L, 2000 + L)
