@@ -16,6 +16,10 @@ Workloads (``--workload``):
             model and, with --exhaustive, the per-instance timed search.
   3d        256^3 centered Hermitian (128 stored in the last axis), M = 384
             per axis, amplitude |k|^-5/3.
+  ns2d      the nonlinear term of 2D incompressible Navier-Stokes in
+            Basdevant's form: velocity spectra u, v of 2048^2 (centered x,
+            Hermitian y, 1024 stored), M = 3072 per axis (2/3 rule), A = B = 2
+            outputs u v and u^2 - v^2, amplitude |k|^-5/3.
 Inputs are seeded synthetic data resident in HBM.
 
 One JSON line per run (rank 0).  Keys beyond the base contract: `roofline`
@@ -189,14 +193,18 @@ def oracle_rate_ragged(budget_s, descs, bins=8):
 def oracle_rate_nd(workload):
     """Convolutions/s of the FP64 explicit zero-padded FFT oracle (numpy) on one full field."""
     from oracle import explicit
+    mult = "product"
     if workload == "2d":
         f = [inputs.spectral_2d(2048, 2048, 3 + a, dtype=np.complex128) for a in range(2)]
         kinds, Ns = ("complex", "complex"), [4096, 4096]
+    elif workload == "ns2d":
+        f = [inputs.hermitian_2d(2048, NS2D_SEED + a, dtype=np.complex128) for a in range(2)]
+        kinds, Ns, mult = ("centered", "hermitian"), [3072, 3072], "basdevant2"
     else:
         f = [inputs.hermitian_3d(256, 5 + a, dtype=np.complex128) for a in range(2)]
         kinds, Ns = ("centered", "centered", "hermitian"), [384, 384, 384]
     t0 = time.perf_counter()
-    explicit.convnd_explicit(f, kinds, Ns)
+    explicit.convnd_explicit(f, kinds, Ns, mult)
     dt = time.perf_counter() - t0
     return 1.0 / dt, 1, f"one full {workload} field, FP64 explicit zero-padded FFT (numpy), {dt:.1f} s"
 
@@ -207,7 +215,9 @@ WORKLOAD_NAMES = {
     "2d": "2d_2048x2048_M4095",
     "ragged": "1d_ragged_10000_L64_65536",
     "3d": "3d_centered_hermitian_256_M384",
+    "ns2d": "2d_navier_stokes_basdevant_hermitian_2048_M3072_A2_B2",
 }
+NS2D_SEED = 7
 
 
 def run_reference(args):
@@ -671,21 +681,98 @@ def run_2d(args, ctx, hd):
 
 
 def e2e_nd(ctx, plan, f, hh):
+    """One convolution per step from pinned host inputs to pinned host
+    outputs (hh: the device output, or the list of B outputs)."""
     torch = ctx.torch
+    hh = list(hh) if isinstance(hh, (list, tuple)) else [hh]
     h_in = [x.cpu().pin_memory() for x in f]
-    h_out = torch.empty(hh.shape, dtype=hh.dtype).pin_memory()
+    h_out = [torch.empty(x.shape, dtype=x.dtype).pin_memory() for x in hh]
     d_in = [torch.empty_like(x) for x in f]
-    d_out = torch.empty_like(hh)
+    d_out = [torch.empty_like(x) for x in hh]
 
     def step():
         for a in range(len(f)):
             d_in[a].copy_(h_in[a], non_blocking=True)
-        plan.convolve(d_in, d_out, stream=ctx.stream)
-        h_out.copy_(d_out, non_blocking=True)
+        plan.convolve(d_in, d_out if len(d_out) > 1 else d_out[0], stream=ctx.stream)
+        for b in range(len(d_out)):
+            h_out[b].copy_(d_out[b], non_blocking=True)
     ms = ctx.time_it(step, 5)
     nb = f[0].numel() * f[0].element_size()
-    return {"value": 1e3 / ms, "unit": "conv/s", "h2d_bytes_per_step": len(f) * nb, "d2h_bytes_per_step": nb,
-            "ms_per_step": ms}
+    return {"value": 1e3 / ms, "unit": "conv/s", "h2d_bytes_per_step": len(f) * nb,
+            "d2h_bytes_per_step": len(d_out) * nb, "ms_per_step": ms}
+
+
+# ----------------------------------------------------------------------------- ns2d
+
+def run_ns2d(args, ctx, hd):
+    """Nonlinear term of 2D incompressible Navier-Stokes (Basdevant form):
+    velocity spectra u, v in, the spectra of u v and u^2 - v^2 out."""
+    from oracle import direct
+    torch = ctx.torch
+    L, M = 2048, 3072
+    H = L // 2
+    # four input/output sets (4 x 64 MiB, more than L2) rotated over the timed calls
+    sets = []
+    for k in range(4):
+        xs = [inputs.hermitian_2d(L, rank_seed(ctx.rank, NS2D_SEED, a) + 100 * k, dtype=np.complex64)
+              for a in range(2)]
+        fk = [torch.from_numpy(x).to(ctx.dev) for x in xs]
+        sets.append((xs, fk, [torch.empty_like(fk[0]) for _ in range(2)]))
+    fs, f, hh = sets[0]
+    g = np.random.default_rng(2)
+    pts = np.stack([g.integers(0, L, 32), g.integers(0, H, 32)], 1)
+    want = direct.convnd_points([x.astype(np.complex128) for x in fs], ("centered", "hermitian"), pts,
+                                "basdevant2")
+    # the inner (Hermitian) axis is a batch of 1D convolutions: tune it on a batch of its rows
+    hd.tune_cache_clear()
+    b_, allc = hd.autotune(4096, reps=3, L=L, M=M, A=2, B=2, kind="hermitian")
+    inner = {"best": {k: b_[k] for k in ("m", "p", "q", "S", "n", "E", "minb", "ms")}, "candidates": len(allc)}
+    plan = hd.Plan([L, L], [M, M], A=2, B=2, kind="hermitian")
+    reps = max(4, args.steps)
+    it = [0]
+
+    def step():
+        _, fk, hk = sets[it[0] % len(sets)]
+        it[0] += 1
+        plan.convolve(fk, hk, stream=ctx.stream)
+    clk = ClockSampler(ctx.local).start()
+    ms = ctx.max_over_ranks(ctx.time_it(step, reps, warm=args.warmup, label="timed"))
+    clocks = clk.stop()
+    plan.convolve(f, hh, stream=ctx.stream)
+    torch.cuda.synchronize()
+    acc = [float(np.linalg.norm(hh[b].cpu().numpy()[tuple(pts.T)] - want[b]) / np.linalg.norm(want[b]))
+           for b in range(2)]
+    e2e = e2e_nd(ctx, plan, f, hh)
+    axes = [plan.axis_params(0), plan.axis_params(1)]
+    scratch = plan.params()["scratch_bytes"]
+    plan.close()
+    hd.tune_cache_clear()
+
+    def cufft():
+        # explicit dealiasing: the velocity fields on the 3072^2 real grid, the two products, back to spectra
+        full = torch.zeros((2, M, M // 2 + 1), dtype=torch.complex64, device=ctx.dev)
+        for a in range(2):
+            c = torch.fft.ifftshift(f[a], dim=0)          # centered x -> FFT order
+            full[a, :H, :H] = c[:H]
+            full[a, -H:, :H] = c[H:]
+        u, v = torch.fft.irfft2(full, s=(M, M))
+        return torch.fft.rfft2(u * v), torch.fft.rfft2((u + v) * (u - v))
+    cu = ctx.time_it(cufft, 5)
+    out = base_line(args, ctx, ctx.job_rate(1, ms), ms, "f32",
+                    "synthetic (seeded real fields, amplitude |k|^-5/3, exact Hermitian symmetry)",
+                    {"workload": WORKLOAD_NAMES["ns2d"], "axes": axes, "inner_axis_autotune": inner,
+                     "scratch_bytes": scratch,
+                     "l2": "4 input/output sets of 64 MiB rotated over the timed calls (256 MiB > L2)"})
+    out.update({"roofline": roofline(4 * L * H * 8, ms, read_traffic("ns2d"), "ns2d plan (all kernels)"),
+                "accuracy": {"rel_l2_sampled": acc, "points": len(pts)},
+                "baselines": {"cufft_f32_explicit_3072^2_real": {"value": 1e3 / cu, "unit": "conv/s", "ms": cu}},
+                # one convolution: outer-axis forward, the inner batch of rows, outer-axis backward
+                "gpu_launches": 3 * reps,
+                "e2e": e2e, "clocks": clocks})
+    if ctx.rank == 0 and not args.no_cpu_baseline:
+        rate, nt, sample = oracle_rate_nd("ns2d")
+        out["cpu_baseline"] = {"value": rate, "unit": "conv/s", "cores": nt, "kind": "oracle", "sample": sample}
+    emit(ctx, out)
 
 
 # ----------------------------------------------------------------------------- 3d
@@ -908,7 +995,7 @@ def main():
     import paper_2303_17510_gb300 as hd
     ctx = Ctx()
     {"batch1d": run_batch1d, "single64": run_single64, "2d": run_2d, "ragged": run_ragged,
-     "3d": run_3d}[args.workload](args, ctx, hd)
+     "3d": run_3d, "ns2d": run_ns2d}[args.workload](args, ctx, hd)
     if ctx.dist is not None:
         ctx.dist.destroy_process_group()
 

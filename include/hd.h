@@ -61,10 +61,17 @@ typedef enum {
 
 enum { HD_COMPLEX = 0, HD_CENTERED = 1, HD_HERMITIAN = 2 };
 enum { HD_F32 = 0, HD_F64 = 1 };
-/* HD_MULT_PRODUCT: A = 2, B = 1, F1*F2 (the binary convolution of Section 2).
+/* The pointwise mult from the A transformed inputs to the B transformed
+ * outputs (Section 2).
+ * HD_MULT_PRODUCT: A = 2, B = 1, F1*F2 (the binary convolution of Section 2).
  * HD_MULT_SUM_PAIRS3: A = 3, B = 1, F1F2 + F2F3 + F3F1, a sum of binary
- * products; it dealiases at the binary bound. */
-enum { HD_MULT_PRODUCT = 0, HD_MULT_SUM_PAIRS3 = 1 };
+ * products; it dealiases at the binary bound.
+ * HD_MULT_BASDEVANT2: A = 2, B = 2, (F1 F2, F1^2 - F2^2): from the velocity
+ * components u, v of a 2D incompressible flow, the products u v and
+ * u^2 - v^2 of its nonlinear term in Basdevant's form (Section 9 counts
+ * A = B = 2).  Binary bound; 1D plans (fused kernel, S up to 4096 FP32 /
+ * 2048 FP64) and 2D/3D plans. */
+enum { HD_MULT_PRODUCT = 0, HD_MULT_SUM_PAIRS3 = 1, HD_MULT_BASDEVANT2 = 2 };
 
 typedef struct hd_plan hd_plan;
 
@@ -75,7 +82,11 @@ typedef struct hd_plan hd_plan;
  * HD_CENTERED otherwise (Section 5, Hermitian data: centered outer axes,
  * Hermitian innermost axis).  m[i] = 0 selects parameters automatically;
  * p[i], q[i] = 0 derive them from m (Eq. pqdef1, Alg. convolve/convolveX,
- * Section 6.1-6.2).  D[i] = 0 selects the residue grouping automatically. */
+ * Section 6.1-6.2).  D[i] = 0 selects the residue grouping automatically:
+ * all residues of an axis in one block.  Fewer residues per block (D[i] < n)
+ * are allowed on the outermost axis only (a middle axis of a 3D plan writes
+ * its outputs over its inputs, so it reads all of them first);
+ * HD_ERR_UNSUPPORTED otherwise. */
 typedef struct {
     int ndim;
     int64_t L[3];
@@ -103,11 +114,13 @@ hd_status hd_derive_params(int kind, int64_t L, int64_t M, int64_t m, int64_t* p
 /* Smallest dealiasing length for L stored-layout outputs (host only):
  * complex 2L-1 (Section 2, M = sum L_i - (A-1)); centered L + floor(L/2);
  * Hermitian the centered bound of the odd expanded length 2 ceil(L/2) - 1.
- * The sum-of-pairs mult has the binary bounds.  Returns -1 on bad input. */
+ * The sum-of-pairs and Basdevant mults have the binary bounds.  Returns -1 on
+ * bad input. */
 int64_t hd_dealias_bound(int kind, int mult, int64_t L);
 
-/* 1D complex FP32 plan.  A = 2 selects HD_MULT_PRODUCT, A = 3
- * HD_MULT_SUM_PAIRS3; B must be 1.  m = 0 selects parameters automatically
+/* 1D complex FP32 plan.  (A, B) = (2, 1) selects HD_MULT_PRODUCT, (3, 1)
+ * HD_MULT_SUM_PAIRS3, (2, 2) HD_MULT_BASDEVANT2; other (A, B) are
+ * HD_ERR_INVALID.  m = 0 selects parameters automatically
  * (tuned cache, learned selector, else a cost model); nonzero m, p, q are
  * validated: p m >= L, q m >= M, and p > 2 requires q % p == 0 (complex).
  * An explicit plan (p = q = 1, m >= M) is always legal.  D = 0 or 1.
@@ -121,8 +134,9 @@ hd_status hd_plan_create(hd_plan** out, int64_t L, int64_t M, int A, int B, int6
 hd_status hd_plan_create_ex(hd_plan** out, const hd_desc* d);
 
 /* One convolution: f[a] (a < A) are device pointers to the A stored
- * inputs, h[b] (b < B) to the B outputs.  h[0] may equal f[0] (in place,
- * allowed because A >= B); other overlaps are not allowed. */
+ * inputs, h[b] (b < B) to the B outputs.  h[b] may equal f[b] for every
+ * b < B (in place, allowed because A >= B: the inputs are read before any
+ * output is written); other overlaps are not allowed. */
 hd_status hd_convolve(const hd_plan* plan, const void* const* f, void* const* h, void* stream);
 
 /* `count` independent convolutions of one plan: instance i of input a

@@ -76,6 +76,38 @@ def spectral_2d(Lx: int, Ly: int, seed: int, alpha: float = 1.0, dtype=np.comple
     return (amp * (u + 1j * v)).astype(dtype)
 
 
+def hermitian_2d(L: int, seed: int, alpha: float = 5.0 / 3.0, dtype=np.complex64) -> np.ndarray:
+    """Stored half of a 2D Hermitian-symmetric field, centered in x (the
+    spectrum of a real field, e.g. one velocity component of a 2D flow).
+
+    A seeded real field of odd size (2*ceil(L/2)-1)^2 through a real-to-complex
+    FFT, scaled by |k|^-alpha (k = 0 scaled by 1), then made exactly symmetric
+    on the y = 0 column: f(-x, 0) = conj f(x, 0) with f(0, 0) real.  For even
+    L the centered index -L/2 is zero.  Returns shape (L, ceil(L/2)).
+    """
+    g = _rng(seed)
+    H = (L + 1) // 2
+    n = 2 * H - 1
+    spec = np.fft.rfft2(g.standard_normal((n, n)))   # (n, H): uncentered kx, ky = 0..H-1
+    kx = np.fft.fftfreq(n, d=1.0 / n)
+    kk = np.sqrt(kx[:, None] ** 2 + np.arange(H, dtype=np.float64)[None, :] ** 2)
+    kk[0, 0] = 1.0
+    spec = spec * kk ** (-alpha) / n
+    out = np.zeros((L, H), dtype=np.complex128)
+    out[kx.astype(np.int64) + L // 2, :] = spec
+    out = out.astype(dtype)
+    c = np.arange(L) - L // 2
+    partner = -c + L // 2
+    valid = (partner >= 0) & (partner < L)
+    col = out[:, 0].copy()
+    take = (c < 0) & valid
+    col[take] = np.conj(col[partner[take]])
+    col[~valid] = 0
+    col[L // 2] = col[L // 2].real
+    out[:, 0] = col
+    return out
+
+
 def hermitian_3d(L: int, seed: int, alpha: float = 5.0 / 3.0, dtype=np.complex64) -> np.ndarray:
     """Stored half of a 3D Hermitian-symmetric field, centered in x and y.
 

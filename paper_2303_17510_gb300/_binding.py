@@ -24,7 +24,18 @@ lib = ctypes.CDLL(LIB_PATH)
 
 KIND = {"complex": 0, "centered": 1, "hermitian": 2}
 DTYPE = {"f32": 0, "f64": 1}
-MULT = {"product": 0, "sum_pairs3": 1}
+MULT = {"product": 0, "sum_pairs3": 1, "basdevant2": 2}
+MULT_AB = {"product": (2, 1), "sum_pairs3": (3, 1), "basdevant2": (2, 2)}   # inputs A, outputs B
+
+
+def _mult_of(A, B, mult):
+    """The mult name (from (A, B) when not given) and B (from the mult when
+    not given); the library validates the counts against the mult."""
+    if mult is None:
+        mult = "basdevant2" if B == 2 else ("product" if A == 2 else "sum_pairs3")
+    if B is None:
+        B = MULT_AB[mult][1]
+    return mult, A, B
 STATUS = {0: "HD_OK", 1: "HD_ERR_INVALID", 2: "HD_ERR_UNSUPPORTED", 3: "HD_ERR_NOMEM", 4: "HD_ERR_CUDA",
           5: "HD_ERR_TIMEOUT", 6: "HD_ERR_ALIASED", 7: "HD_ERR_SCRATCH_LIMIT"}
 _i64 = ctypes.c_int64
@@ -154,7 +165,8 @@ def _stream(stream) -> int:
     return int(stream.cuda_stream)
 
 
-def make_desc(L, M, A=2, B=1, m=0, p=0, q=0, D=0, kind="complex", dtype="f32", mult=None, ndim=None):
+def make_desc(L, M, A=2, B=None, m=0, p=0, q=0, D=0, kind="complex", dtype="f32", mult=None, ndim=None):
+    mult, A, B = _mult_of(A, B, mult)
     Ls = list(L) if isinstance(L, (list, tuple)) else [L]
     Ms = list(M) if isinstance(M, (list, tuple)) else [M]
     ms = list(m) if isinstance(m, (list, tuple)) else [m] * len(Ls)
@@ -162,8 +174,6 @@ def make_desc(L, M, A=2, B=1, m=0, p=0, q=0, D=0, kind="complex", dtype="f32", m
     qs = list(q) if isinstance(q, (list, tuple)) else [q] * len(Ls)
     Ds = list(D) if isinstance(D, (list, tuple)) else [D] * len(Ls)
     nd = ndim or len(Ls)
-    if mult is None:
-        mult = "product" if A == 2 else "sum_pairs3"
     d = hd_desc()
     d.ndim = nd
     for i in range(nd):
@@ -215,10 +225,9 @@ def tune_cache_clear():
 class Plan:
     """A convolution plan (owns device twiddle tables and scratch)."""
 
-    def __init__(self, L, M, A=2, B=1, m=0, p=0, q=0, D=0, kind="complex", dtype="f32", mult=None, ndim=None,
+    def __init__(self, L, M, A=2, B=None, m=0, p=0, q=0, D=0, kind="complex", dtype="f32", mult=None, ndim=None,
                  candidate=None):
-        if mult is None:
-            mult = "product" if A == 2 else "sum_pairs3"
+        mult, A, B = _mult_of(A, B, mult)
         d = make_desc(L, M, A, B, m, p, q, D, kind, dtype, mult, ndim)
         self._h = _vp()
         if candidate is None:
@@ -250,7 +259,8 @@ class Plan:
         return dict(m=m.value, p=p.value, q=q.value, D=D.value, S=S.value, n=n.value)
 
     def convolve(self, fs, h, stream=None):
-        """One convolution: fs = A device arrays (tensors or addresses), h = output."""
+        """One convolution: fs = A device arrays (tensors or addresses), h = the
+        output (or a list of the B outputs)."""
         fa = (_vp * self.A)(*[_ptr(x) for x in fs])
         ha = (_vp * self.B)(*[_ptr(h)] if not isinstance(h, (list, tuple)) else [_ptr(x) for x in h])
         _check(lib.hd_convolve(self._h, fa, ha, _stream(stream)), "hd_convolve")

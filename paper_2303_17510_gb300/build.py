@@ -83,7 +83,8 @@ def build(verbose: bool = False, jobs: int | None = None, extra=None) -> str:
 
 def _build_locked(verbose, jobs, extra) -> str:
     extra = list(extra or [])
-    srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    # the kernel instantiation units take longest: start them first
+    srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")), key=lambda p: ("hd_conv1d_" not in p, p))
     hdr = ""
     jobs = jobs or max(1, min(len(srcs), os.cpu_count() or 1))
     with cf.ThreadPoolExecutor(max_workers=jobs) as ex:

@@ -141,8 +141,8 @@ int64_t split_rows(int dtype) { return max_fused_S(dtype); }
 
 bool split_supported(int dtype, int kind, int mult, int64_t S, int nb) {
     (void)kind;
-    (void)mult;
     (void)nb;
+    if (mult == HD_MULT_BASDEVANT2) return false;   // the split row kernels have one output
     const int64_t S2 = split_rows(dtype);
     if (!is_pow2(S) || S <= max_fused_S(dtype)) return false;
     const int64_t S1 = S / S2;
@@ -203,12 +203,25 @@ hd_status validate_axis(int kind, int mult, int64_t L, int64_t M, int64_t m, int
     return HD_OK;
 }
 
-int default_minb(int dtype, int64_t S) { return (dtype == HD_F32 && S <= 2048) ? 2 : 1; }
+// Two CTAs per SM (128 registers) for FP32 transforms up to 2048; the
+// two-output mult holds twice the residue sums and keeps 255 registers.
+int default_minb(int dtype, int64_t S, int mult) {
+    return (dtype == HD_F32 && S <= 2048 && mult != HD_MULT_BASDEVANT2) ? 2 : 1;
+}
 
 bool fused_supported(int dtype, int kind, int mult, int64_t S, int nb, int64_t Ls, bool comp, int E, int minb) {
     if (!is_pow2(S) || S < 2 || S > max_fused_S(dtype)) return false;
     Conv1dCfg c{dtype, kind, mult, nb, (int)S, E, comp, minb};
     return conv1d_available(c, (int)staged_row(Ls));
+}
+
+bool mult_counts_ok(int mult, int A, int B) {
+    return (mult == HD_MULT_PRODUCT && A == 2 && B == 1) || (mult == HD_MULT_SUM_PAIRS3 && A == 3 && B == 1) ||
+           (mult == HD_MULT_BASDEVANT2 && A == 2 && B == 2);
+}
+
+int kernel_mult(int mult) {
+    return mult == HD_MULT_BASDEVANT2 ? MULT_BASD2 : (mult == HD_MULT_SUM_PAIRS3 ? MULT_PAIRS3 : MULT_PRODUCT);
 }
 
 // FFT work of one convolution in units of S log2 S (model used when no
@@ -229,6 +242,16 @@ namespace hd {
 
 #define HD_SEL(fn, c, ...)                                                                   \
     do {                                                                                     \
+        if (c.mult == MULT_BASD2) {                                                          \
+            if (c.dtype == HD_F32) {                                                         \
+                if (c.kind == KIND_COMPLEX) return fn##_f32_complex_b2(__VA_ARGS__);         \
+                if (c.kind == KIND_CENTERED) return fn##_f32_centered_b2(__VA_ARGS__);       \
+                return fn##_f32_hermitian_b2(__VA_ARGS__);                                   \
+            }                                                                                \
+            if (c.kind == KIND_COMPLEX) return fn##_f64_complex_b2(__VA_ARGS__);             \
+            if (c.kind == KIND_CENTERED) return fn##_f64_centered_b2(__VA_ARGS__);           \
+            return fn##_f64_hermitian_b2(__VA_ARGS__);                                       \
+        }                                                                                    \
         if (c.dtype == HD_F32) {                                                             \
             if (c.kind == KIND_COMPLEX) return fn##_f32_complex(__VA_ARGS__);                \
             if (c.kind == KIND_CENTERED) return fn##_f32_centered(__VA_ARGS__);              \
@@ -262,9 +285,12 @@ hd_status hd_device_status(void) {
         cudaGetLastError();
         return HD_ERR_CUDA;
     }
-    const int e[6] = {conv1d_take_error_f32_complex(), conv1d_take_error_f32_centered(),
-                      conv1d_take_error_f32_hermitian(), conv1d_take_error_f64_complex(),
-                      conv1d_take_error_f64_centered(), conv1d_take_error_f64_hermitian()};
+    const int e[12] = {conv1d_take_error_f32_complex(),     conv1d_take_error_f32_centered(),
+                       conv1d_take_error_f32_hermitian(),   conv1d_take_error_f64_complex(),
+                       conv1d_take_error_f64_centered(),    conv1d_take_error_f64_hermitian(),
+                       conv1d_take_error_f32_complex_b2(),  conv1d_take_error_f32_centered_b2(),
+                       conv1d_take_error_f32_hermitian_b2(), conv1d_take_error_f64_complex_b2(),
+                       conv1d_take_error_f64_centered_b2(), conv1d_take_error_f64_hermitian_b2()};
     hd_status st = HD_OK;
     for (int v : e) {
         if (v < 0) return HD_ERR_CUDA;
@@ -314,7 +340,8 @@ hd_status hd_derive_params(int kind, int64_t L, int64_t M, int64_t m, int64_t* p
 }
 
 int64_t hd_dealias_bound(int kind, int mult, int64_t L) {
-    if (L <= 0 || (mult != HD_MULT_PRODUCT && mult != HD_MULT_SUM_PAIRS3)) return -1;
+    // every output of every mult is a (signed) sum of binary products
+    if (L <= 0 || (mult != HD_MULT_PRODUCT && mult != HD_MULT_SUM_PAIRS3 && mult != HD_MULT_BASDEVANT2)) return -1;
     if (kind == HD_COMPLEX) return 2 * L - 1;
     if (kind == HD_CENTERED) return L + L / 2;
     if (kind == HD_HERMITIAN) {
@@ -328,7 +355,7 @@ hd_status hd_plan_create(hd_plan** out, int64_t L, int64_t M, int A, int B, int6
                          int D) {
     if (!out) return HD_ERR_INVALID;
     *out = nullptr;
-    if (B != 1 || (A != 2 && A != 3)) return HD_ERR_INVALID;
+    if (!((A == 2 && (B == 1 || B == 2)) || (A == 3 && B == 1))) return HD_ERR_INVALID;
     hd_desc d;
     std::memset(&d, 0, sizeof(d));
     d.ndim = 1;
@@ -338,7 +365,7 @@ hd_status hd_plan_create(hd_plan** out, int64_t L, int64_t M, int A, int B, int6
     d.B = B;
     d.kind = HD_COMPLEX;
     d.dtype = HD_F32;
-    d.mult = A == 2 ? HD_MULT_PRODUCT : HD_MULT_SUM_PAIRS3;
+    d.mult = B == 2 ? HD_MULT_BASDEVANT2 : (A == 2 ? HD_MULT_PRODUCT : HD_MULT_SUM_PAIRS3);
     d.m[0] = m;
     d.p[0] = p;
     d.q[0] = q;
@@ -375,7 +402,8 @@ hd_status hd_convolve_batched(const hd_plan* plan, int64_t count, const void* co
     if (count == 0) return HD_OK;
     for (int a = 0; a < plan->A; ++a)
         if (!f[a]) return HD_ERR_INVALID;
-    if (!h[0]) return HD_ERR_INVALID;
+    for (int b = 0; b < plan->B; ++b)
+        if (!h[b]) return HD_ERR_INVALID;
     if (count > 1 && batch_stride < plan->instance_elems) return HD_ERR_INVALID;
     return hd::plan_execute(const_cast<hd_plan*>(plan), count, f, h, batch_stride, (cudaStream_t)stream);
 }

@@ -9,7 +9,8 @@
 // The columns' size-S FFTs run in shared memory interleaved column by column
 // (CST = TY), which keeps the exchanges free of bank conflicts.
 //
-// Work buffer layout: F[a][inst][r'][slot][col], slot = tau + T e labels the
+// Work buffer layout: F[a][inst][r'][slot][col] (a < max(A, B): the inner
+// sub-convolutions write output b over input b), slot = tau + T e labels the
 // spectral value held in register e (any fixed labeling of the outer
 // frequencies works: the inner sub-convolution treats every slot row
 // independently).  For each outer instance the rows F[a][inst][r'][slot][:] are
@@ -23,13 +24,13 @@ namespace hd {
 struct ColArgs {
     const void* f[3];     // colfwd: A input bases; element (inst, x, col) at f + inst*inst_stride + x*pitch + col
     void* work;           // F[a][inst][r'][slot][col]
-    void* h;              // colbwd: output base, same layout as the inputs
+    void* h[kMaxOut];     // colbwd: B output bases, same layout as the inputs
     int64_t inst_stride;  // elements between outer instances
     int64_t count;        // outer instances
     int64_t pitch;        // elements between consecutive x of one column
     int64_t ncols;        // columns per instance
     int L, H;             // stored axis length, centered offset floor(L/2)
-    int n, S, A;          // residues of the axis, transform size, inputs
+    int n, S, A, B;       // residues of the axis, transform size, inputs, outputs
     int r0, nr;           // residue block handled by this call
     int accumulate;       // colbwd: add to h (blocks after the first)
     const void* twS;      // FFT pass twiddles of (S, E)
@@ -103,9 +104,9 @@ __global__ void __launch_bounds__(ColShape<S, E>::THREADS) col_forward(const __g
     }
 }
 
-// Backward: for every residue of the block, inverse FFT along x of the
-// sub-convolution results (held in input 0's part of the work buffer), the
-// conjugate twist, and the residue sum; one store (or add) per output.
+// Backward: output blockIdx.y; for every residue of the block, inverse FFT
+// along x of the sub-convolution results (held in part b of the work buffer),
+// the conjugate twist, and the residue sum; one store (or add) per output.
 template <class R, int S, int E, int KIND, bool COMP>
 __global__ void __launch_bounds__(ColShape<S, E>::THREADS) col_backward(const __grid_constant__ ColArgs a) {
     using T = cplx<R>;
@@ -117,6 +118,7 @@ __global__ void __launch_bounds__(ColShape<S, E>::THREADS) col_backward(const __
     const int tau = threadIdx.x / TY;
     const int64_t col = (int64_t)blockIdx.x * TY + y;
     const bool valid = col < a.ncols;
+    const int ob = blockIdx.y;
     const int64_t inst = blockIdx.z;
     T* sm = reinterpret_cast<T*>(smem_raw) + y;
     const TwGlobal<T> tw{static_cast<const T*>(a.twS)};
@@ -132,7 +134,8 @@ __global__ void __launch_bounds__(ColShape<S, E>::THREADS) col_backward(const __
         const int r = a.r0 + rr;
         T cr = ldtw(twN + (int64_t)a.n * S + r);
         if constexpr (KIND == KIND_CENTERED) cr = cconj(cr);
-        const T* g = static_cast<const T*>(a.work) + (inst * a.nr + rr) * (int64_t)S * a.ncols + (valid ? col : 0);
+        const T* g = static_cast<const T*>(a.work) + (((int64_t)ob * a.count + inst) * a.nr + rr) * (int64_t)S * a.ncols +
+                     (valid ? col : 0);
         T v[E];
 #pragma unroll
         for (int e = 0; e < E; ++e) v[e] = valid ? g[(int64_t)(tau + TT * e) * a.ncols] : czero<T>();
@@ -150,7 +153,7 @@ __global__ void __launch_bounds__(ColShape<S, E>::THREADS) col_backward(const __
         }
     }
     if (!valid) return;
-    T* hout = static_cast<T*>(a.h) + inst * a.inst_stride + col;
+    T* hout = static_cast<T*>(a.h[ob]) + inst * a.inst_stride + col;
     const R sc = R(a.invN);
 #pragma unroll
     for (int e = 0; e < E; ++e) {

@@ -34,7 +34,7 @@ cudaError_t col_run(const ColArgs& a, cudaStream_t st) {
             cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
         }
-        k<<<dim3(gx, 1, (unsigned)a.count), CS::THREADS, smem, st>>>(a);
+        k<<<dim3(gx, (unsigned)a.B, (unsigned)a.count), CS::THREADS, smem, st>>>(a);
     }
     return cudaGetLastError();
 }

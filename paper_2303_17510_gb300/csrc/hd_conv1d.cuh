@@ -30,6 +30,9 @@
 // imaginary parts separately; the inverse of the product splits back by
 // y_j = (Y_j + conj Y_{S-j})/2 and (Y_j - conj Y_{S-j})/(2i).
 //
+// mult maps the A transformed inputs to B transformed outputs pointwise
+// (Section 2); each output has its own inverse transform and residue sum.
+//
 // FP32 accumulation over residues is compensated (TwoSum) from 8 residues on
 // (COMP), plain below; FP64 is plain.
 #pragma once
@@ -39,11 +42,53 @@
 namespace hd {
 
 enum { KIND_COMPLEX = 0, KIND_CENTERED = 1, KIND_HERMITIAN = 2 };
-enum { MULT_PRODUCT = 0, MULT_PAIRS3 = 1 };
+enum { MULT_PRODUCT = 0, MULT_PAIRS3 = 1, MULT_BASD2 = 2 };
+
+// Inputs A and outputs B of each mult; NX = max(A, B) exchange buffers.
+//   MULT_PRODUCT  A = 2, B = 1:  F1 F2
+//   MULT_PAIRS3   A = 3, B = 1:  F1 F2 + F2 F3 + F3 F1
+//   MULT_BASD2    A = 2, B = 2:  (F1 F2, F1^2 - F2^2), the nonlinear terms of
+//                 2D incompressible Navier-Stokes in Basdevant's form
+//                 (velocity components in; Section 9 counts A = B = 2)
+template <int MULT>
+struct MultShape {
+    static constexpr int A = MULT == MULT_PAIRS3 ? 3 : 2;
+    static constexpr int B = MULT == MULT_BASD2 ? 2 : 1;
+    static constexpr int NX = A > B ? A : B;
+};
+constexpr int kMaxOut = 2;
+
+// arithmetic of mult on complex or real values
+__device__ __forceinline__ float xmul(float a, float b) { return a * b; }
+__device__ __forceinline__ double xmul(double a, double b) { return a * b; }
+__device__ __forceinline__ float2 xmul(float2 a, float2 b) { return cmul(a, b); }
+__device__ __forceinline__ double2 xmul(double2 a, double2 b) { return cmul(a, b); }
+__device__ __forceinline__ float xadd(float a, float b) { return a + b; }
+__device__ __forceinline__ double xadd(double a, double b) { return a + b; }
+__device__ __forceinline__ float2 xadd(float2 a, float2 b) { return cadd(a, b); }
+__device__ __forceinline__ double2 xadd(double2 a, double2 b) { return cadd(a, b); }
+__device__ __forceinline__ float xsub(float a, float b) { return a - b; }
+__device__ __forceinline__ double xsub(double a, double b) { return a - b; }
+__device__ __forceinline__ float2 xsub(float2 a, float2 b) { return csub(a, b); }
+__device__ __forceinline__ double2 xsub(double2 a, double2 b) { return csub(a, b); }
+
+// mult at one point: x[a * XS] (a < A) -> y[b * YS] (b < B).  X is a complex
+// value, or a real one for the Hermitian pairs (their spectra are real).
+template <int MULT, int XS, int YS, class X>
+__device__ __forceinline__ void mult_point(const X* x, X* y) {
+    if constexpr (MULT == MULT_PRODUCT) {
+        y[0] = xmul(x[0], x[XS]);
+    } else if constexpr (MULT == MULT_PAIRS3) {   // F1F2 + F2F3 + F3F1 = F1 F2 + F3 (F1 + F2)
+        y[0] = xadd(xmul(x[0], x[XS]), xmul(x[2 * XS], xadd(x[0], x[XS])));
+    } else {                                       // F1 F2, F1^2 - F2^2 = (F1 + F2)(F1 - F2)
+        y[0] = xmul(x[0], x[XS]);
+        y[YS] = xmul(xadd(x[0], x[XS]), xsub(x[0], x[XS]));
+    }
+}
 
 struct ConvArgs {
     const void* f[3];   // A input bases (device)
-    void* h;            // output base (device)
+    void* h[kMaxOut];   // B output bases (device)
     int64_t stride;     // elements between instances
     int64_t count;      // instances
     int L;              // stored length of complex/centered data; full length for Hermitian
@@ -119,7 +164,8 @@ struct ConvLaunch {
 // Body of one fused convolution for one thread group: instance `inst` of a,
 // thread tau of the group, the group's staging area st (A * ls_pad values)
 // and exchange buffers sm (A * SMEM values).  Every thread of the CTA runs the
-// same sequence of barriers (groups of one CTA share n).  FFT twiddles are
+// same sequence of barriers (groups of one CTA share n).  sm holds NX = max(A, B)
+// exchange buffers of SMEM values.  FFT twiddles are
 // read through the read-only data cache (a shared-memory table measured
 // slower: it competes with the exchanges for shared-memory bandwidth).
 struct NoHook {
@@ -136,7 +182,8 @@ __device__ __forceinline__ void conv1d_body(const ConvArgs& a, int64_t inst, boo
     using T = cplx<R>;
     using Sh = FftShape<S, E>;
     constexpr int TT = Sh::T;
-    constexpr int A = (MULT == MULT_PRODUCT) ? 2 : 3;
+    constexpr int A = MultShape<MULT>::A;
+    constexpr int B = MultShape<MULT>::B;
     const T* twN = static_cast<const T*>(a.twN);
     const TwGlobal<T> twS{static_cast<const T*>(a.twS)};
 
@@ -153,20 +200,21 @@ __device__ __forceinline__ void conv1d_body(const ConvArgs& a, int64_t inst, boo
         __syncthreads();
     }
 
-    R s0[2 * E], c0[COMP ? 2 * E : 1];
-    R s1[NB == 2 ? 2 * E : 1], c1[(NB == 2 && COMP) ? 2 * E : 1];
+    // residue sums of output b at [b * 2E + 2e (+1)]
+    R s0[B * 2 * E], c0[COMP ? B * 2 * E : 1];
+    R s1[NB == 2 ? B * 2 * E : 1], c1[(NB == 2 && COMP) ? B * 2 * E : 1];
 #pragma unroll
-    for (int e = 0; e < 2 * E; ++e) s0[e] = R(0);
+    for (int e = 0; e < B * 2 * E; ++e) s0[e] = R(0);
     if constexpr (COMP) {
 #pragma unroll
-        for (int e = 0; e < 2 * E; ++e) c0[e] = R(0);
+        for (int e = 0; e < B * 2 * E; ++e) c0[e] = R(0);
     }
     if constexpr (NB == 2) {
 #pragma unroll
-        for (int e = 0; e < 2 * E; ++e) s1[e] = R(0);
+        for (int e = 0; e < B * 2 * E; ++e) s1[e] = R(0);
         if constexpr (COMP) {
 #pragma unroll
-            for (int e = 0; e < 2 * E; ++e) c1[e] = R(0);
+            for (int e = 0; e < B * 2 * E; ++e) c1[e] = R(0);
         }
     }
     R dummy = R(0);
@@ -199,26 +247,25 @@ __device__ __forceinline__ void conv1d_body(const ConvArgs& a, int64_t inst, boo
             }
             fft_forward<S, E, A>(v, sm, twS, tau);
             if (r == a.n - 1) consumed();
-            T p[E];
+            T p[B * E];
 #pragma unroll
-            for (int e = 0; e < E; ++e) {
-                if constexpr (MULT == MULT_PRODUCT) {
-                    p[e] = cmul(v[e], v[E + e]);
-                } else {   // F1F2 + F2F3 + F3F1 = F1 F2 + F3 (F1 + F2)
-                    p[e] = cadd(cmul(v[e], v[E + e]), cmul(v[2 * E + e], cadd(v[e], v[E + e])));
-                }
-            }
-            fft_inverse<S, E, 1>(p, sm, twS, tau);
+            for (int e = 0; e < E; ++e) mult_point<MULT, E, E>(v + e, p + e);
+            fft_inverse<S, E, B>(p, sm, twS, tau);
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const int j = tau + TT * e;
-                const T y = R0 ? p[e] : cmulc(p[e], ldtw(twr + j));        // zeta_N^{-r j} y_j
-                acc_add<R, COMP>(s0[2 * e], COMP ? c0[2 * e] : dummy, y.x);
-                acc_add<R, COMP>(s0[2 * e + 1], COMP ? c0[2 * e + 1] : dummy, y.y);
-                if constexpr (NB == 2) {
-                    const T y1 = R0 ? y : cmulc(y, cr);                 // block 1: extra zeta_N^{-r o}
-                    acc_add<R, COMP>(s1[2 * e], COMP ? c1[2 * e] : dummy, y1.x);
-                    acc_add<R, COMP>(s1[2 * e + 1], COMP ? c1[2 * e + 1] : dummy, y1.y);
+                const T tw = R0 ? mk<T>(1, 0) : ldtw(twr + j);
+#pragma unroll
+                for (int b = 0; b < B; ++b) {
+                    const int o = b * 2 * E + 2 * e;
+                    const T y = R0 ? p[b * E + e] : cmulc(p[b * E + e], tw);   // zeta_N^{-r j} y_j
+                    acc_add<R, COMP>(s0[o], COMP ? c0[o] : dummy, y.x);
+                    acc_add<R, COMP>(s0[o + 1], COMP ? c0[o + 1] : dummy, y.y);
+                    if constexpr (NB == 2) {
+                        const T y1 = R0 ? y : cmulc(y, cr);             // block 1: extra zeta_N^{-r o}
+                        acc_add<R, COMP>(s1[o], COMP ? c1[o] : dummy, y1.x);
+                        acc_add<R, COMP>(s1[o + 1], COMP ? c1[o + 1] : dummy, y1.y);
+                    }
                 }
             }
         };
@@ -251,36 +298,48 @@ __device__ __forceinline__ void conv1d_body(const ConvArgs& a, int64_t inst, boo
             }
             fft_forward<S, E, A>(v, sm, twS, tau);
             if (r1 + 2 >= a.n) consumed();
-            // real parts carry residue r1, imaginary parts residue r2
-            T p[E];
+            // real parts carry residue r1, imaginary parts residue r2: mult on each
+            T p[B * E];
 #pragma unroll
             for (int e = 0; e < E; ++e) {
-                const T x0 = v[e], x1 = v[E + e];
-                if constexpr (MULT == MULT_PRODUCT) {
-                    p[e] = mk<T>(x0.x * x1.x, x0.y * x1.y);
-                } else {
-                    const T x2 = v[2 * E + e];
-                    p[e] = mk<T>(x0.x * x1.x + x2.x * (x0.x + x1.x), x0.y * x1.y + x2.y * (x0.y + x1.y));
-                }
-            }
-            fft_inverse<S, E, 1>(p, sm, twS, tau);
-            // split the two Hermitian inverses: needs Y_{S-j}
+                R xr[A], xi[A], yr[B], yi[B];
 #pragma unroll
-            for (int e = 0; e < E; ++e) sm[padidx(tau + TT * e)] = p[e];
+                for (int aa = 0; aa < A; ++aa) {
+                    xr[aa] = v[aa * E + e].x;
+                    xi[aa] = v[aa * E + e].y;
+                }
+                mult_point<MULT, 1, 1>(xr, yr);
+                mult_point<MULT, 1, 1>(xi, yi);
+#pragma unroll
+                for (int b = 0; b < B; ++b) p[b * E + e] = mk<T>(yr[b], yi[b]);
+            }
+            fft_inverse<S, E, B>(p, sm, twS, tau);
+            // split the two Hermitian inverses: needs Y_{S-j} (output b in exchange buffer b)
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+#pragma unroll
+                for (int b = 0; b < B; ++b) sm[b * Sh::SMEM + padidx(tau + TT * e)] = p[b * E + e];
+            }
             __syncthreads();
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const int j = tau + TT * e;
-                const T ym = sm[padidx((S - j) & (S - 1))];
-                const T yj = p[e];
-                const R hf = R(0.5);
-                const T g1 = mk<T>((yj.x + ym.x) * hf, (yj.y - ym.y) * hf);   // (Y_j + conj Y_{S-j}) / 2
-                const T d = mk<T>(yj.x - ym.x, yj.y + ym.y);                  // Y_j - conj Y_{S-j}
-                const T g2 = mk<T>(d.y * hf, -d.x * hf);                       // d / (2i)
-                T y = R0 ? g1 : cmulc(g1, ldtw(twr1 + j));
-                if (has2) y = cadd(y, cmulc(g2, ldtw(twr2 + j)));
-                acc_add<R, COMP>(s0[2 * e], COMP ? c0[2 * e] : dummy, y.x);
-                acc_add<R, COMP>(s0[2 * e + 1], COMP ? c0[2 * e + 1] : dummy, y.y);
+                const T t1 = R0 ? mk<T>(1, 0) : ldtw(twr1 + j);
+                const T t2 = has2 ? ldtw(twr2 + j) : czero<T>();
+#pragma unroll
+                for (int b = 0; b < B; ++b) {
+                    const int o = b * 2 * E + 2 * e;
+                    const T ym = sm[b * Sh::SMEM + padidx((S - j) & (S - 1))];
+                    const T yj = p[b * E + e];
+                    const R hf = R(0.5);
+                    const T g1 = mk<T>((yj.x + ym.x) * hf, (yj.y - ym.y) * hf);   // (Y_j + conj Y_{S-j}) / 2
+                    const T d = mk<T>(yj.x - ym.x, yj.y + ym.y);                  // Y_j - conj Y_{S-j}
+                    const T g2 = mk<T>(d.y * hf, -d.x * hf);                       // d / (2i)
+                    T y = R0 ? g1 : cmulc(g1, t1);
+                    if (has2) y = cadd(y, cmulc(g2, t2));
+                    acc_add<R, COMP>(s0[o], COMP ? c0[o] : dummy, y.x);
+                    acc_add<R, COMP>(s0[o + 1], COMP ? c0[o + 1] : dummy, y.y);
+                }
             }
             __syncthreads();
         };
@@ -289,32 +348,36 @@ __device__ __forceinline__ void conv1d_body(const ConvArgs& a, int64_t inst, boo
     }
 
     if (!valid) return;
-    T* hout = static_cast<T*>(a.h) + inst * a.stride;
     const R sc = R(a.invN);
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int j = tau + TT * e;
-        const R x0 = COMP ? s0[2 * e] + c0[2 * e] : s0[2 * e];
-        const R y0 = COMP ? s0[2 * e + 1] + c0[2 * e + 1] : s0[2 * e + 1];
-        const T o0 = mk<T>(x0 * sc, y0 * sc);
-        T o1 = czero<T>();
-        if constexpr (NB == 2) {
-            const R x1 = COMP ? s1[2 * e] + c1[2 * e] : s1[2 * e];
-            const R y1 = COMP ? s1[2 * e + 1] + c1[2 * e + 1] : s1[2 * e + 1];
-            o1 = mk<T>(x1 * sc, y1 * sc);
-        }
-        if constexpr (KIND == KIND_COMPLEX) {
-            if (j < a.L) __stcs(hout + j, o0);
+    for (int b = 0; b < B; ++b) {
+        T* hout = static_cast<T*>(a.h[b]) + inst * a.stride;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int j = tau + TT * e;
+            const int o = b * 2 * E + 2 * e;
+            const R x0 = COMP ? s0[o] + c0[o] : s0[o];
+            const R y0 = COMP ? s0[o + 1] + c0[o + 1] : s0[o + 1];
+            const T o0 = mk<T>(x0 * sc, y0 * sc);
+            T o1 = czero<T>();
             if constexpr (NB == 2) {
-                if (j + S < a.L) __stcs(hout + j + S, o1);
+                const R x1 = COMP ? s1[o] + c1[o] : s1[o];
+                const R y1 = COMP ? s1[o + 1] + c1[o + 1] : s1[o + 1];
+                o1 = mk<T>(x1 * sc, y1 * sc);
             }
-        } else if constexpr (KIND == KIND_CENTERED) {
-            if (j < a.L - a.H) __stcs(hout + j + a.H, o0);
-            if constexpr (NB == 2) {
-                if (j >= S - a.H) __stcs(hout + j - S + a.H, o1);
+            if constexpr (KIND == KIND_COMPLEX) {
+                if (j < a.L) __stcs(hout + j, o0);
+                if constexpr (NB == 2) {
+                    if (j + S < a.L) __stcs(hout + j + S, o1);
+                }
+            } else if constexpr (KIND == KIND_CENTERED) {
+                if (j < a.L - a.H) __stcs(hout + j + a.H, o0);
+                if constexpr (NB == 2) {
+                    if (j >= S - a.H) __stcs(hout + j - S + a.H, o1);
+                }
+            } else {
+                if (j < a.Ls) __stcs(hout + j, o0);
             }
-        } else {
-            if (j < a.Ls) __stcs(hout + j, o0);
         }
     }
 }
@@ -328,12 +391,13 @@ __global__ void __launch_bounds__(ConvLaunch<S, E>::MAXT, MINB) conv1d_kernel(co
     using T = cplx<R>;
     using Sh = FftShape<S, E>;
     constexpr int TT = Sh::T;
-    constexpr int A = (MULT == MULT_PRODUCT) ? 2 : 3;
+    constexpr int A = MultShape<MULT>::A;
+    constexpr int NX = MultShape<MULT>::NX;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int G = blockDim.x / TT;
     const int g = threadIdx.x / TT;
     const int tau = threadIdx.x - g * TT;
-    T* st = reinterpret_cast<T*>(smem_raw) + (size_t)g * (A * a.ls_pad + A * Sh::SMEM);
+    T* st = reinterpret_cast<T*>(smem_raw) + (size_t)g * (A * a.ls_pad + NX * Sh::SMEM);
     T* sm = st + A * a.ls_pad;
     const int64_t inst = (int64_t)blockIdx.x * G + g;
     conv1d_body<R, S, E, KIND, MULT, NB, COMP>(a, inst, inst < a.count, tau, st, sm);
@@ -406,7 +470,8 @@ __global__ void __launch_bounds__(ConvLaunch<S, E>::MAXT, MINB) conv1d_kernel_pi
     using T = cplx<R>;
     using Sh = FftShape<S, E>;
     constexpr int TT = Sh::T;
-    constexpr int A = (MULT == MULT_PRODUCT) ? 2 : 3;
+    constexpr int A = MultShape<MULT>::A;
+    constexpr int NX = MultShape<MULT>::NX;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ int s_ok;
@@ -415,7 +480,7 @@ __global__ void __launch_bounds__(ConvLaunch<S, E>::MAXT, MINB) conv1d_kernel_pi
     const int tau = threadIdx.x - g * TT;
     const size_t stage_elems = (size_t)G * A * a.ls_pad;          // one staging buffer (all groups)
     T* stage0 = reinterpret_cast<T*>(smem_raw);
-    T* sm = stage0 + NBUF * stage_elems + (size_t)g * A * Sh::SMEM;
+    T* sm = stage0 + NBUF * stage_elems + (size_t)g * NX * Sh::SMEM;
     const int64_t nsteps = (a.count + G - 1) / G;                    // CTA steps over the batch
     const uint32_t row_bytes = (uint32_t)(a.Ls * sizeof(T));
 

@@ -1,7 +1,9 @@
-// Fused 1D convolution kernels: f32, centered data (instantiation unit).
+// Fused 1D convolution kernels: f32, centered data, the single-output mults (instantiation unit).
 #define HD_REAL float
 #define HD_KIND hd::KIND_CENTERED
 #define HD_DT f32
 #define HD_KN centered
-#define HD_VARIANTS(X) X(2, 2, 2) X(4, 4, 2) X(8, 8, 2) X(16, 8, 2) X(32, 8, 2) X(64, 8, 2) X(128, 8, 2) X(256, 8, 2) X(512, 8, 2) X(1024, 8, 2) X(2048, 8, 2) X(4096, 8, 1) X(512, 8, 1) X(1024, 8, 1) X(2048, 8, 1) X(512, 4, 1) X(1024, 4, 1) X(2048, 4, 1) X(256, 16, 1) X(512, 16, 1) X(1024, 16, 1) X(2048, 16, 1) X(4096, 16, 1)
+#define HD_VARIANTS HD_VARIANTS_F32
+#define HD_UNIT_MULTS(Y, ...) Y(MULT_PRODUCT, __VA_ARGS__) Y(MULT_PAIRS3, __VA_ARGS__)
+#include "hd_conv1d_variants.h"
 #include "hd_conv1d_tu.cuh"

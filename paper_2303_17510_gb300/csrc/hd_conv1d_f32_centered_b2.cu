@@ -1,0 +1,9 @@
+// Fused 1D convolution kernels: f32, centered data, the two-output mult (Basdevant 2D) (instantiation unit).
+#define HD_REAL float
+#define HD_KIND hd::KIND_CENTERED
+#define HD_DT f32
+#define HD_KN centered_b2
+#define HD_VARIANTS HD_VARIANTS_F32
+#define HD_UNIT_MULTS(Y, ...) Y(MULT_BASD2, __VA_ARGS__)
+#include "hd_conv1d_variants.h"
+#include "hd_conv1d_tu.cuh"

@@ -1,6 +1,7 @@
 // hd_conv1d_tu.cuh -- instantiation table of the fused 1D kernels for one
-// (dtype, kind) pair.  Included by the hd_conv1d_<dtype>_<kind>.cu files with
-// HD_REAL, HD_KIND, HD_DT, HD_KN and HD_SE_EXTRA defined.
+// (dtype, kind, mult set).  Included by the hd_conv1d_<dtype>_<kind>[_b2].cu
+// files with HD_REAL, HD_KIND, HD_DT, HD_KN, HD_VARIANTS and HD_UNIT_MULTS
+// defined (HD_UNIT_MULTS(Y, ...) calls Y(mult, ...) for each mult of the unit).
 #include <algorithm>
 #include <cstdint>
 #include <cstdlib>
@@ -13,8 +14,8 @@ namespace {
 
 template <class R, int S, int E, int MULT>
 size_t group_smem(int ls_pad) {
-    constexpr int A = MULT == MULT_PRODUCT ? 2 : 3;
-    return size_t(A) * (size_t(ls_pad) + FftShape<S, E>::SMEM) * sizeof(cplx<R>);
+    using MS = MultShape<MULT>;
+    return (size_t(MS::A) * size_t(ls_pad) + size_t(MS::NX) * FftShape<S, E>::SMEM) * sizeof(cplx<R>);
 }
 
 template <class R, int S, int E, int MULT>
@@ -53,7 +54,8 @@ int* pipe_err_ptr() {
 template <class R, int S, int E, int KIND, int MULT, int NB, bool COMP, int MINB>
 cudaError_t launch_pipe(const ConvArgs& a0, cudaStream_t st, bool* used) {
     constexpr int T = S / E;
-    constexpr int A = MULT == MULT_PRODUCT ? 2 : 3;
+    constexpr int A = MultShape<MULT>::A;
+    constexpr int NX = MultShape<MULT>::NX;
     constexpr int NBUF = MINB == 1 ? 2 : 1;
     *used = false;
     static const bool enabled = [] {
@@ -67,7 +69,7 @@ cudaError_t launch_pipe(const ConvArgs& a0, cudaStream_t st, bool* used) {
     if ((a0.stride * esz) % 16 != 0 || (a0.Ls * esz) % 16 != 0 || (a0.ls_pad * esz) % 16 != 0) return cudaSuccess;
     int G = 256 / T;
     if (G < 1) G = 1;
-    const size_t fft = size_t(A) * FftShape<S, E>::SMEM * esz;
+    const size_t fft = size_t(NX) * FftShape<S, E>::SMEM * esz;
     const size_t stg = size_t(A) * a0.ls_pad * esz;
     while (G > 1 && G * (NBUF * stg + fft) > kMaxSmemPerBlock - 64) --G;
     const size_t smem = size_t(G) * (NBUF * stg + fft);
@@ -158,17 +160,16 @@ bool fits(int ls_pad) {
 }  // namespace
 
 // Kernel variants compiled for this dtype, as (S, E, MINB): HD_VARIANTS is
-// defined by the including unit.
-#define HD_COMBOS(SS, EE, MB, FN, ...)                                                                       \
-    if (c.S == SS && c.E == EE && c.minb == MB) {                                                            \
-        if (c.mult == MULT_PRODUCT && c.nb == 1 && !c.comp) return FN<SS, EE, MB, MULT_PRODUCT, 1, false>(__VA_ARGS__); \
-        if (c.mult == MULT_PRODUCT && c.nb == 1 && c.comp) return FN<SS, EE, MB, MULT_PRODUCT, 1, true>(__VA_ARGS__);   \
-        if (c.mult == MULT_PAIRS3 && c.nb == 1 && !c.comp) return FN<SS, EE, MB, MULT_PAIRS3, 1, false>(__VA_ARGS__);   \
-        if (c.mult == MULT_PAIRS3 && c.nb == 1 && c.comp) return FN<SS, EE, MB, MULT_PAIRS3, 1, true>(__VA_ARGS__);     \
-        if (c.mult == MULT_PRODUCT && c.nb == 2 && !c.comp) return FN<SS, EE, MB, MULT_PRODUCT, 2, false>(__VA_ARGS__); \
-        if (c.mult == MULT_PRODUCT && c.nb == 2 && c.comp) return FN<SS, EE, MB, MULT_PRODUCT, 2, true>(__VA_ARGS__);   \
-        if (c.mult == MULT_PAIRS3 && c.nb == 2 && !c.comp) return FN<SS, EE, MB, MULT_PAIRS3, 2, false>(__VA_ARGS__);   \
-        if (c.mult == MULT_PAIRS3 && c.nb == 2 && c.comp) return FN<SS, EE, MB, MULT_PAIRS3, 2, true>(__VA_ARGS__);     \
+// defined by the including unit; every variant is compiled for each mult of
+// the unit, both folded-block counts and both accumulations (combo_ok prunes).
+#define HD_MULT_COMBOS(MU, SS, EE, MB, FN, ...)                                                          \
+    if (c.mult == MU && c.nb == 1 && !c.comp) return FN<SS, EE, MB, MU, 1, false>(__VA_ARGS__);          \
+    if (c.mult == MU && c.nb == 1 && c.comp) return FN<SS, EE, MB, MU, 1, true>(__VA_ARGS__);            \
+    if (c.mult == MU && c.nb == 2 && !c.comp) return FN<SS, EE, MB, MU, 2, false>(__VA_ARGS__);          \
+    if (c.mult == MU && c.nb == 2 && c.comp) return FN<SS, EE, MB, MU, 2, true>(__VA_ARGS__);
+#define HD_COMBOS(SS, EE, MB, FN, ...)                                                                   \
+    if (c.S == SS && c.E == EE && c.minb == MB) {                                                        \
+        HD_UNIT_MULTS(HD_MULT_COMBOS, SS, EE, MB, FN, __VA_ARGS__)                                       \
     }
 
 #define HD_LAUNCH_CASE(SS, EE, MB) HD_COMBOS(SS, EE, MB, pick, a, st)

@@ -44,7 +44,8 @@ cudaError_t col_launch_f64(const ColArgs& a, int kind, bool comp, bool fwd, cuda
 int col_E_of_f32(int S);
 int col_E_of_f64(int S);
 
-// per translation unit entry points (dtype x kind)
+// per translation unit entry points (dtype x kind x mult set: the
+// single-output mults, and the two-output one in the _b2 units)
 #define HD_DECL_TU(DT, KN)                                                                                   \
     bool conv1d_available_##DT##_##KN(const Conv1dCfg& c, int ls_pad);                                                    \
     cudaError_t conv1d_launch_##DT##_##KN(const Conv1dCfg& c, const ConvArgs& a, cudaStream_t st);            \
@@ -58,6 +59,12 @@ HD_DECL_TU(f32, hermitian)
 HD_DECL_TU(f64, complex)
 HD_DECL_TU(f64, centered)
 HD_DECL_TU(f64, hermitian)
+HD_DECL_TU(f32, complex_b2)
+HD_DECL_TU(f32, centered_b2)
+HD_DECL_TU(f32, hermitian_b2)
+HD_DECL_TU(f64, complex_b2)
+HD_DECL_TU(f64, centered_b2)
+HD_DECL_TU(f64, hermitian_b2)
 #undef HD_DECL_TU
 
 }  // namespace hd

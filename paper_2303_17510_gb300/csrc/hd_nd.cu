@@ -73,6 +73,7 @@ ColArgs make_col_args(const hd_plan& pl, const AxisPlan& ax, int level, int64_t 
     a.n = (int)ax.n;
     a.S = (int)ax.S;
     a.A = pl.A;
+    a.B = pl.B;
     a.r0 = r0;
     a.nr = nr;
     a.twS = ax.twS;
@@ -88,9 +89,10 @@ int64_t ncols_of(const hd_plan& pl, int level) {
     return c;
 }
 
-// Convolves `cnt` instances of the sub-array of axes level..ndim-1.
-hd_status exec_level(const hd_plan& pl, int level, int64_t cnt, const void* const* f, int64_t inst_stride, void* h,
-                     cudaStream_t st) {
+// Convolves `cnt` instances of the sub-array of axes level..ndim-1: A inputs
+// f, B outputs h.
+hd_status exec_level(const hd_plan& pl, int level, int64_t cnt, const void* const* f, int64_t inst_stride,
+                     void* const* h, cudaStream_t st) {
     const AxisPlan& ax = pl.ax[level];
     if (level == pl.ndim - 1) return rows_execute(pl, ax, cnt, f, h, inst_stride, pl.scratch, st);
     const int64_t ncols = ncols_of(pl, level);
@@ -104,13 +106,16 @@ hd_status exec_level(const hd_plan& pl, int level, int64_t cnt, const void* cons
         cudaError_t e = pl.dtype == HD_F64 ? col_launch_f64(a, outer_kind, false, true, st)
                                            : col_launch_f32(a, outer_kind, false, true, st);
         if (e != cudaSuccess) return HD_ERR_CUDA;
-        // the transformed slices: A batches of cnt * nrb * S sub-arrays of ncols values
+        // the transformed slices: A batches of cnt * nrb * S sub-arrays of ncols
+        // values; the sub-convolutions write output b over part b
         const int64_t sub = cnt * nrb * ax.S;
         const void* g[3];
+        void* gh[kMaxOut];
         for (int i = 0; i < pl.A; ++i) g[i] = static_cast<const char*>(pl.work[level]) + (size_t)i * sub * ncols * esz;
-        hd_status s2 = exec_level(pl, level + 1, sub, g, ncols, pl.work[level], st);
+        for (int b = 0; b < pl.B; ++b) gh[b] = static_cast<char*>(pl.work[level]) + (size_t)b * sub * ncols * esz;
+        hd_status s2 = exec_level(pl, level + 1, sub, g, ncols, gh, st);
         if (s2 != HD_OK) return s2;
-        a.h = h;
+        for (int b = 0; b < pl.B; ++b) a.h[b] = h[b];
         a.accumulate = r0 > 0;
         e = pl.dtype == HD_F64 ? col_launch_f64(a, outer_kind, false, false, st)
                                : col_launch_f32(a, outer_kind, false, false, st);
@@ -125,9 +130,7 @@ hd_status plan_create_nd(hd_plan** out, const hd_desc* d) {
     const int nd = d->ndim;
     if (d->kind < HD_COMPLEX || d->kind > HD_HERMITIAN) return HD_ERR_INVALID;
     if (d->dtype != HD_F32 && d->dtype != HD_F64) return HD_ERR_INVALID;
-    if (d->B != 1) return HD_ERR_INVALID;
-    if (!((d->mult == HD_MULT_PRODUCT && d->A == 2) || (d->mult == HD_MULT_SUM_PAIRS3 && d->A == 3)))
-        return HD_ERR_INVALID;
+    if (!mult_counts_ok(d->mult, d->A, d->B)) return HD_ERR_INVALID;
     for (int i = 0; i < nd; ++i) {
         if (d->L[i] <= 0 || d->M[i] <= 0 || d->m[i] < 0 || d->p[i] < 0 || d->q[i] < 0 || d->D[i] < 0)
             return HD_ERR_INVALID;
@@ -161,6 +164,9 @@ hd_status plan_create_nd(hd_plan** out, const hd_desc* d) {
                 ax.E = col_E_of(d->dtype, ax.S);
                 ax.comp = false;
                 ax.D = d->D[i] > 0 ? d->D[i] : (int)ax.n;
+                // a middle axis writes its outputs over its inputs in the parent's work
+                // buffer, so all of its residues must be read before the first is written
+                if (i > 0 && ax.D < ax.n) st = HD_ERR_UNSUPPORTED;
             }
         } else if (d->m[i] == 0) {
             // the innermost axis is a batch of 1D convolutions: tuning cache, selector, cost model
@@ -198,7 +204,7 @@ hd_status plan_create_nd(hd_plan** out, const hd_desc* d) {
         }
         if (st == HD_OK) st = upload_twists(ax.S, ax.n, d->dtype, &ax.twN);
     }
-    // work buffers: level k holds A * count_k * D_k * S_k * ncols_k values, count_0 = 1
+    // work buffers: level k holds max(A, B) * count_k * D_k * S_k * ncols_k values, count_0 = 1
     int64_t inst = 1;
     pl->instance_elems = 1;
     for (int i = 0; i < nd; ++i) pl->instance_elems *= pl->ax[i].Ls;
@@ -206,7 +212,7 @@ hd_status plan_create_nd(hd_plan** out, const hd_desc* d) {
     for (int k = 0; k < nd - 1 && st == HD_OK; ++k) {
         const AxisPlan& ax = pl->ax[k];
         const int64_t nr = ax.D;
-        const int64_t elems = (int64_t)d->A * inst * nr * ax.S * ncols_of(*pl, k);
+        const int64_t elems = (int64_t)(d->A > d->B ? d->A : d->B) * inst * nr * ax.S * ncols_of(*pl, k);
         if (inst * nr * ax.S > 65535 * 64) {
             st = HD_ERR_UNSUPPORTED;
             break;
@@ -247,8 +253,9 @@ hd_status plan_execute_nd(hd_plan* pl, int64_t count, const void* const* f, void
     const size_t esz = pl->dtype == HD_F64 ? 16 : 8;
     for (int64_t i = 0; i < count; ++i) {
         const void* fi[3];
+        void* hi[kMaxOut];
         for (int a = 0; a < pl->A; ++a) fi[a] = static_cast<const char*>(f[a]) + (size_t)(i * stride) * esz;
-        void* hi = static_cast<char*>(h[0]) + (size_t)(i * stride) * esz;
+        for (int b = 0; b < pl->B; ++b) hi[b] = static_cast<char*>(h[b]) + (size_t)(i * stride) * esz;
         hd_status s2 = exec_level(*pl, 0, 1, fi, pl->instance_elems, hi, st);
         if (s2 != HD_OK) return s2;
     }

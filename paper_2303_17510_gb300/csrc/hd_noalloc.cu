@@ -44,7 +44,8 @@ extern "C" hd_status hd_convolve_batched_noalloc(const hd_plan* plan, int64_t co
     if (ax.path != hd::PATH_SPLIT) return HD_ERR_UNSUPPORTED;
     for (int a = 0; a < plan->A; ++a)
         if (!f[a]) return HD_ERR_INVALID;
-    if (!h[0]) return HD_ERR_INVALID;
+    for (int b = 0; b < plan->B; ++b)
+        if (!h[b]) return HD_ERR_INVALID;
     if (count > 1 && batch_stride < plan->instance_elems) return HD_ERR_INVALID;
     const size_t esz = plan->dtype == HD_F64 ? 16 : 8;
     const size_t per = (size_t)plan->A * (size_t)ax.n * (size_t)ax.S * esz;

@@ -98,7 +98,7 @@ hd_status fill_axis(int dtype, int kind, int mult, int64_t L, int64_t M, int64_t
     ax->nb = nb;
     ax->E = S < 8 ? (int)S : 8;
     ax->comp = dtype == HD_F32 && comp_default(n);
-    ax->minb = default_minb(dtype, S);
+    ax->minb = default_minb(dtype, S, mult);
     if (fused_supported(dtype, kind, mult, S, nb, ax->Ls, ax->comp, ax->E, ax->minb)) {
         ax->path = PATH_FUSED;
         return HD_OK;
@@ -151,9 +151,7 @@ hd_status check_desc_1d(const hd_desc* d) {
     if (d->ndim != 1) return HD_ERR_UNSUPPORTED;
     if (d->kind < HD_COMPLEX || d->kind > HD_HERMITIAN) return HD_ERR_INVALID;
     if (d->dtype != HD_F32 && d->dtype != HD_F64) return HD_ERR_INVALID;
-    if (d->B != 1) return HD_ERR_INVALID;
-    if (!((d->mult == HD_MULT_PRODUCT && d->A == 2) || (d->mult == HD_MULT_SUM_PAIRS3 && d->A == 3)))
-        return HD_ERR_INVALID;
+    if (!mult_counts_ok(d->mult, d->A, d->B)) return HD_ERR_INVALID;
     if (d->L[0] <= 0 || d->M[0] <= 0 || d->m[0] < 0 || d->p[0] < 0 || d->q[0] < 0) return HD_ERR_INVALID;
     if (d->M[0] < hd_dealias_bound(d->kind, d->mult, d->L[0])) return HD_ERR_ALIASED;
     return HD_OK;
@@ -237,7 +235,7 @@ hd_status axis_from_candidate(const hd_desc* d, const hd_candidate* c, AxisPlan*
 hd_status auto_axis(const hd_desc* d, AxisPlan* ax) {
     hd_candidate c;
     if (cache_lookup(d, &c) && axis_from_candidate(d, &c, ax) == HD_OK) return HD_OK;
-    if (selector_installed()) {
+    if (selector_installed() && d->B == 1) {   // trained on single-output mults
         std::vector<hd_candidate> cands;
         enumerate_candidates(d, &cands);
         std::vector<int> pick, conf;
@@ -276,7 +274,7 @@ ConvArgs make_conv_args(const hd_plan& pl, const AxisPlan& ax, int64_t count, co
     ConvArgs a;
     std::memset(&a, 0, sizeof(a));
     for (int i = 0; i < pl.A && i < 3; ++i) a.f[i] = f[i];
-    a.h = h ? h[0] : nullptr;
+    for (int b = 0; b < pl.B && b < kMaxOut; ++b) a.h[b] = h ? h[b] : nullptr;
     a.stride = stride;
     a.count = count;
     a.L = (int)ax.L;
@@ -295,7 +293,7 @@ Conv1dCfg fused_cfg(const hd_plan& pl, const AxisPlan& ax) {
     Conv1dCfg c;
     c.dtype = pl.dtype;
     c.kind = ax.kind;
-    c.mult = pl.mult == HD_MULT_PRODUCT ? MULT_PRODUCT : MULT_PAIRS3;
+    c.mult = kernel_mult(pl.mult);
     c.nb = ax.nb;
     c.S = (int)ax.S;
     c.E = ax.E;
@@ -331,7 +329,7 @@ SplitArgs make_split_args(const hd_plan& pl, const AxisPlan& ax, int64_t first, 
 
 hd_status split_execute(const hd_plan& pl, const AxisPlan& ax, int64_t count, const void* const* f, void* const* h,
                         int64_t stride, void* work, int64_t chunk, cudaStream_t st) {
-    const int mult = pl.mult == HD_MULT_PRODUCT ? MULT_PRODUCT : MULT_PAIRS3;
+    const int mult = kernel_mult(pl.mult);
     for (int64_t first = 0; first < count; first += chunk) {
         const int64_t cnt = count - first < chunk ? count - first : chunk;
         SplitArgs a = make_split_args(pl, ax, first, cnt, f, h, stride, work);
@@ -342,11 +340,10 @@ hd_status split_execute(const hd_plan& pl, const AxisPlan& ax, int64_t count, co
     return HD_OK;
 }
 
-hd_status rows_execute(const hd_plan& pl, const AxisPlan& ax, int64_t count, const void* const* f, void* h,
-                       int64_t stride, void* scratch, cudaStream_t st) {
-    void* hh[1] = {h};
-    if (ax.path == PATH_SPLIT) return split_execute(pl, ax, count, f, hh, stride, scratch, ax.chunk, st);
-    ConvArgs a = make_conv_args(pl, ax, count, f, hh, stride);
+hd_status rows_execute(const hd_plan& pl, const AxisPlan& ax, int64_t count, const void* const* f,
+                       void* const* h, int64_t stride, void* scratch, cudaStream_t st) {
+    if (ax.path == PATH_SPLIT) return split_execute(pl, ax, count, f, h, stride, scratch, ax.chunk, st);
+    ConvArgs a = make_conv_args(pl, ax, count, f, h, stride);
     return conv1d_launch(fused_cfg(pl, ax), a, st) == cudaSuccess ? HD_OK : HD_ERR_CUDA;
 }
 

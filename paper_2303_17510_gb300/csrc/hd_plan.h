@@ -50,7 +50,7 @@ void axis_geometry(int kind, int64_t L, int64_t m, int64_t p, int64_t q, int64_t
 hd_status validate_axis(int kind, int mult, int64_t L, int64_t M, int64_t m, int64_t p, int64_t q, int64_t* S,
                         int64_t* n, int* nb);
 bool fused_supported(int dtype, int kind, int mult, int64_t S, int nb, int64_t Ls, bool comp, int E, int minb);
-int default_minb(int dtype, int64_t S);
+int default_minb(int dtype, int64_t S, int mult);
 // split path (transforms larger than one CTA): S = S1 * S2, S2 the fused limit, S1 <= 16
 bool split_supported(int dtype, int kind, int mult, int64_t S, int nb);
 int64_t split_rows(int dtype);
@@ -58,6 +58,10 @@ hd_status upload_split_twiddles(int64_t S1, int64_t S2, int dtype, void** dev);
 // staged row length in shared memory for Ls stored values (even: 16-byte rows)
 inline int64_t staged_row(int64_t Ls) { return (Ls + 1) & ~int64_t(1); }
 double cost_model(int kind, int A, int B, int64_t S, int64_t n);
+// true when (A, B) are the input and output counts of the mult HD_MULT_*
+bool mult_counts_ok(int mult, int A, int B);
+// the kernels' mult (MULT_*) of a mult HD_MULT_*
+int kernel_mult(int mult);
 
 }  // namespace hd
 
@@ -107,9 +111,10 @@ void ragged_destroy(hd_plan* pl);
 hd_status plan_create_nd(hd_plan** out, const hd_desc* d);
 hd_status plan_execute_nd(hd_plan* pl, int64_t count, const void* const* f, void* const* h, int64_t stride,
                           cudaStream_t st);
-// batched 1D convolution of rows with axis plan ax (fused or split path)
-hd_status rows_execute(const hd_plan& pl, const AxisPlan& ax, int64_t count, const void* const* f, void* h,
-                       int64_t stride, void* scratch, cudaStream_t st);
+// batched 1D convolution of rows with axis plan ax (fused or split path):
+// the A inputs f, the B outputs h
+hd_status rows_execute(const hd_plan& pl, const AxisPlan& ax, int64_t count, const void* const* f,
+                       void* const* h, int64_t stride, void* scratch, cudaStream_t st);
 
 // Plan for an explicit candidate (kernel variant included).
 hd_status plan_create_from(hd_plan** out, const hd_desc* d, const hd_candidate* c);

@@ -36,7 +36,8 @@ __device__ __noinline__ void fused_tile(const RaggedArgs& ra, const RTile& t, un
     constexpr int TT = S / E;
     constexpr int KIND = KINDNB == 2 ? KIND_CENTERED : KIND_COMPLEX;
     constexpr int NB = KINDNB == 0 ? 1 : 2;
-    constexpr int A = MULT == MULT_PRODUCT ? 2 : 3;
+    constexpr int A = MultShape<MULT>::A;
+    static_assert(MultShape<MULT>::B == 1, "single-output mults only");
     const int g = threadIdx.x / TT;
     const int tau = threadIdx.x - g * TT;
     const bool valid = g < t.count;

@@ -136,7 +136,8 @@ __device__ __forceinline__ ConvArgs conv_args_of(const RInst& r) {
     a.f[0] = r.f[0];
     a.f[1] = r.f[1];
     a.f[2] = r.f[2];
-    a.h = r.h;
+    a.h[0] = r.h;   // one output (B = 1)
+    a.h[1] = nullptr;
     a.stride = 0;
     a.count = 1;
     a.L = r.L;

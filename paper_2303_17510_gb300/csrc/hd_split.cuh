@@ -152,7 +152,8 @@ __device__ __forceinline__ void split_row_body(const SplitArgs& a, int64_t row, 
     using T = cplx<R>;
     using Sh = FftShape<S2, E>;
     constexpr int TT = Sh::T;
-    constexpr int A = (MULT == MULT_PRODUCT) ? 2 : 3;
+    constexpr int A = MultShape<MULT>::A;
+    static_assert(MultShape<MULT>::B == 1, "single-output mults only");
     const int k1 = (int)(row % a.S1);
     const int64_t rr = row / a.S1;
     const int r = (int)(rr % a.n);
@@ -206,7 +207,8 @@ __global__ void __launch_bounds__(ConvLaunch<S2, E>::MAXT) split_row(const __gri
     using T = cplx<R>;
     using Sh = FftShape<S2, E>;
     constexpr int TT = Sh::T;
-    constexpr int A = (MULT == MULT_PRODUCT) ? 2 : 3;
+    constexpr int A = MultShape<MULT>::A;
+    static_assert(MultShape<MULT>::B == 1, "single-output mults only");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int G = blockDim.x / TT;
     const int g = threadIdx.x / TT;

@@ -13,7 +13,8 @@ cudaError_t run_split(const SplitArgs& a, cudaStream_t st) {
     constexpr int S2 = HD_S2;
     constexpr int E = 8;
     constexpr int T = S2 / E;
-    constexpr int A = MULT == MULT_PRODUCT ? 2 : 3;
+    constexpr int A = MultShape<MULT>::A;
+    static_assert(MultShape<MULT>::B == 1, "single-output mults only");
     const int64_t n1 = a.count * a.A * a.n * (int64_t)S2;
     if (n1 <= 0) return cudaSuccess;
     split_colfwd<R, S1, KIND><<<(unsigned)((n1 + 255) / 256), 256, 0, st>>>(a);

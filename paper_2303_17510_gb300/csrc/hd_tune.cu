@@ -20,8 +20,7 @@ bool desc_ok_1d(const hd_desc* d) {
     if (!d || d->ndim != 1) return false;
     if (d->kind < HD_COMPLEX || d->kind > HD_HERMITIAN) return false;
     if (d->dtype != HD_F32 && d->dtype != HD_F64) return false;
-    if (d->B != 1) return false;
-    if (!((d->mult == HD_MULT_PRODUCT && d->A == 2) || (d->mult == HD_MULT_SUM_PAIRS3 && d->A == 3))) return false;
+    if (!mult_counts_ok(d->mult, d->A, d->B)) return false;
     return d->L[0] > 0 && d->M[0] > 0;
 }
 
@@ -214,7 +213,7 @@ hd_status hd_autotune(const hd_desc* d, int64_t count, int reps, hd_candidate* o
     const size_t bytes = (size_t)count * (size_t)Ls * esz;
     void* buf[4] = {nullptr, nullptr, nullptr, nullptr};
     hd_status st = HD_OK;
-    for (int a = 0; a <= d->A && st == HD_OK; ++a) {
+    for (int a = 0; a < d->A + d->B && st == HD_OK; ++a) {   // A inputs, B outputs (at most 4)
         if (cudaMalloc(&buf[a], bytes) != cudaSuccess) st = HD_ERR_NOMEM;
         else if (cudaMemset(buf[a], 0, bytes) != cudaSuccess) st = HD_ERR_CUDA;
     }
@@ -229,7 +228,7 @@ hd_status hd_autotune(const hd_desc* d, int64_t count, int reps, hd_candidate* o
             continue;
         }
         const void* f[3] = {buf[0], buf[1], buf[2]};
-        void* h[1] = {buf[d->A]};
+        void* h[2] = {buf[d->A], d->B > 1 ? buf[d->A + 1] : nullptr};
         t.clear();
         for (int r = 0; r < 2 + reps && st == HD_OK; ++r) {
             cudaEventRecord(e0, 0);

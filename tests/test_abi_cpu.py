@@ -52,7 +52,7 @@ def test_paper_examples_through_abi(hd):
 
 
 @pytest.mark.parametrize("kind", ["complex", "centered", "hermitian"])
-@pytest.mark.parametrize("mult", ["product", "sum_pairs3"])
+@pytest.mark.parametrize("mult", ["product", "sum_pairs3", "basdevant2"])
 def test_dealias_bound_matches_oracle(hd, kind, mult):
     for L in range(1, 300):
         assert hd.dealias_bound(kind, L, mult) == params.dealias_bound(kind, L, mult)
@@ -92,3 +92,24 @@ def test_enumerated_candidates_are_legal(hd, kind, dtype):
             # at least one candidate with the paper's own p for the largest legal m
     with pytest.raises(hd.HdError):
         hd.enumerate_candidates(L=0, M=5)
+
+
+def test_mult_counts_validated(hd):
+    """(A, B) must be the counts of the mult; the two-output mult has no split
+    path (transforms beyond the fused kernel) and no ragged form.  All of
+    these are refused before any device work."""
+    for A, B, mult in ((3, 2, None), (2, 2, "product"), (3, 1, "basdevant2"), (2, 3, None), (1, 1, "product")):
+        with pytest.raises(hd.HdError) as e:
+            hd.Plan(100, 199, A=A, B=B, mult=mult)
+        assert e.value.name == "HD_ERR_INVALID", (A, B, mult)
+    with pytest.raises(hd.HdError) as e:
+        hd.Plan(40000, 79999, A=2, B=2)
+    assert e.value.name == "HD_ERR_UNSUPPORTED"
+    import ctypes
+    out = ctypes.c_void_p()
+    assert hd.lib.hd_plan_create(ctypes.byref(out), 100, 199, 3, 2, 0, 0, 0, 0) == 1   # HD_ERR_INVALID
+    assert hd.lib.hd_plan_create(ctypes.byref(out), 100, 199, 2, 3, 0, 0, 0, 0) == 1
+    assert out.value is None
+    cands = hd.enumerate_candidates(L=20000, M=39999, A=2, B=2)
+    assert cands == []
+    assert hd.enumerate_candidates(L=4096, M=8191, A=2, B=2)
