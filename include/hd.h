@@ -70,7 +70,8 @@ enum { HD_F32 = 0, HD_F64 = 1 };
  * components u, v of a 2D incompressible flow, the products u v and
  * u^2 - v^2 of its nonlinear term in Basdevant's form (Section 9 counts
  * A = B = 2).  Binary bound; 1D plans (fused kernel, S up to 4096 FP32 /
- * 2048 FP64) and 2D/3D plans. */
+ * 2048 FP64; FP32 from S = 512 on unless a candidate of hd_enumerate_candidates
+ * is given) and 2D/3D plans. */
 enum { HD_MULT_PRODUCT = 0, HD_MULT_SUM_PAIRS3 = 1, HD_MULT_BASDEVANT2 = 2 };
 
 typedef struct hd_plan hd_plan;
