@@ -105,6 +105,13 @@ def test_mult_counts_validated(hd):
     with pytest.raises(hd.HdError) as e:
         hd.Plan(40000, 79999, A=2, B=2)
     assert e.value.name == "HD_ERR_UNSUPPORTED"
+    # the default variant of FP32 two-output plans (E = 8, 255 registers) starts at S = 512;
+    # smaller transforms are reachable through enumerated candidates
+    with pytest.raises(hd.HdError) as e:
+        hd.Plan(300, 450, m=128, A=2, B=2, kind="centered")
+    assert e.value.name == "HD_ERR_UNSUPPORTED"
+    small = [c for c in hd.enumerate_candidates(L=300, M=450, A=2, B=2, kind="centered") if c["S"] < 512]
+    assert small and not any(c["E"] == 8 and c["minb"] == 1 for c in small)
     import ctypes
     out = ctypes.c_void_p()
     assert hd.lib.hd_plan_create(ctypes.byref(out), 100, 199, 3, 2, 0, 0, 0, 0) == 1   # HD_ERR_INVALID
