@@ -309,8 +309,9 @@ __device__ __forceinline__ void fft_exchange(T* v, T* sm, int tau) {
     constexpr int Qn = Sh::sub(k + 1) / Rn;
     // Pad elements per 16: 1, or 2 for the radix-8 reads with 1 < Qn < 16, whose
     // half-warps otherwise meet two words in one bank (checked on the CPU for
-    // every exchange of E = 8 and 16: the writes and reads of each exchange
-    // are then conflict-free).  Column tiles (CST > 1) keep 1.
+    // every exchange of E = 8 and 16, tests/test_fft_exchange_cpu.py: the
+    // writes and reads of each exchange are then conflict-free, and every
+    // index stays below SMEM).  Column tiles (CST > 1) keep 1.
     constexpr int PADM = (CST == 1 && Rn == 8 && Qn > 1 && Qn < 16) ? 2 : 1;
     static_assert(PADM == 1 || E == 8, "two pad elements per 16 only fit the E = 8 buffers");
     auto padk = [](int a) { return a + (a >> 4) * PADM; };
