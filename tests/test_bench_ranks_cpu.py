@@ -71,13 +71,14 @@ def test_reference_arm_only_rank0_prints(monkeypatch):
     assert buf.getvalue() == ""
 
 
-def test_reference_arm_json_line(monkeypatch, capsys):
+@pytest.mark.parametrize("workload", ["single64", "ns2d"])
+def test_reference_arm_json_line(monkeypatch, capsys, workload):
     """The reference arm (the FP64 oracle on the host cores) prints one JSON
     line with the contract's keys, its own cpu_baseline and a zero-copy e2e."""
     sys.path.insert(0, ROOT)
     import bench
     monkeypatch.setenv("RANK", "0")
-    args = type("A", (), dict(steps=1, warmup=3, gpus=1, workload="single64", ragged_n=10000))()
+    args = type("A", (), dict(steps=1, warmup=3, gpus=1, workload=workload, ragged_n=10000))()
     bench.run_reference(args)
     line = capsys.readouterr().out.strip().splitlines()
     assert len(line) == 1
@@ -88,4 +89,4 @@ def test_reference_arm_json_line(monkeypatch, capsys):
     assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
-    assert d["config"]["workload"] == "1d_single_L1024_M2047_f64"
+    assert d["config"]["workload"] == bench.WORKLOAD_NAMES[workload]
