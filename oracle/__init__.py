@@ -10,8 +10,10 @@ examples.
 
 Modules
   direct   -- the definition: truncated linear convolution (complex, centered,
-              Hermitian; 1D and separable N-D; sampled output points).  Exact on
-              integer-valued inputs.  Section 2 (problem statement), Sections 3-5.
+              Hermitian; 1D and separable N-D; sampled output points), for every
+              mult as signed sums of binary products (the Basdevant forms of
+              Section 9 have B > 1 outputs).  Exact on integer-valued inputs.
+              Section 2 (problem statement), Sections 3-5.
   params   -- parameter derivation p, q, n of Alg. convolve / convolveX and the
               inner-loop redefinition (Eq. pqdef1, Section 6.1, Section 6.2);
               dealiasing bounds; work-memory formulas (Section 4/5, memory).
