@@ -29,7 +29,8 @@ MEASURED_PEAKS.json), `alu` (FFT flop rate, 5 S log2 S per transform, vs the
 FP32 CUDA-core peak at the sampled clock), `cpu_baseline` (the FP64 oracle on
 this host's cores, bounded sample), `e2e` (the same metric through the C ABI
 from pinned host buffers), `baselines` (cuFFT explicit zero padding, the FP64
-paths), `accuracy` (rel-L2 / max-abs against the FP64 oracle).
+paths; for the 1D batch also the FP64 explicit FFT convolution on one host
+thread), `accuracy` (rel-L2 / max-abs against the FP64 oracle).
 
 ``--impl reference`` runs the oracle arm of the selected workload on the
 host cores (bounded samples), same metric and unit.
@@ -157,6 +158,26 @@ def oracle_rate_1d(budget_s, L, kinds, integer=False):
         done += per
         i += 1
     return done / t_total, nt, f"{done} convolutions of L={L} ({'/'.join(kinds)}), FP64 direct sum, {nt} threads"
+
+
+def oracle_rate_explicit_1d(budget_s, L, subs):
+    """Convolutions/s of the FP64 explicit zero-padded FFT convolution (numpy,
+    the paper's comparison method) on one host thread, over the sub-configs
+    (kind, M) in turn; the padded length is M (centered) or the next power of
+    two (complex), as in the cuFFT baseline."""
+    from oracle import explicit
+    done, t_total, i = 0, 0.0, 0
+    while t_total < budget_s:
+        kind, M = subs[i % len(subs)]
+        N = M if kind != "complex" else 1 << (M - 1).bit_length()
+        fs = [inputs.uniform_complex(L, 700 + 2 * i + a) for a in range(2)]
+        t0 = time.perf_counter()
+        explicit.convnd_explicit(fs, (kind,), [N])
+        t_total += time.perf_counter() - t0
+        done += 1
+        i += 1
+    return done / t_total, (f"{done} convolutions of L={L} ({'/'.join(k for k, _ in subs)}), "
+                            "FP64 explicit zero-padded FFT (numpy), one thread")
 
 
 def oracle_rate_ragged(budget_s, descs, bins=8):
@@ -551,6 +572,9 @@ def run_batch1d(args, ctx, hd):
     if ctx.rank == 0 and not args.no_cpu_baseline:
         rate, nt, sample = oracle_rate_1d(10.0, L1D, [k for k, _ in SUBS])
         out["cpu_baseline"] = {"value": rate, "unit": "conv/s", "cores": nt, "kind": "oracle", "sample": sample}
+        rate_x, sample_x = oracle_rate_explicit_1d(3.0, L1D, SUBS)
+        out["baselines"]["cpu_fp64_explicit_fft"] = {"value": rate_x, "unit": "conv/s", "cores": 1,
+                                                     "sample": sample_x}
     emit(ctx, out)
     for p in plans:
         p.close()

@@ -90,3 +90,12 @@ def test_reference_arm_json_line(monkeypatch, capsys, workload):
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["config"]["workload"] == bench.WORKLOAD_NAMES[workload]
+
+
+def test_explicit_fft_cpu_rate():
+    """The second CPU timing of the 1D batch (the paper's explicit method in
+    FP64 on the host): a positive rate over the sub-configurations."""
+    sys.path.insert(0, ROOT)
+    import bench
+    rate, sample = bench.oracle_rate_explicit_1d(0.2, bench.L1D, bench.SUBS)
+    assert rate > 0 and "explicit" in sample
