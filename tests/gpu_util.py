@@ -11,6 +11,19 @@ def rel_l2(got, ref):
     return float(np.linalg.norm(got - ref) / nr)
 
 
+def rel_l2_rows(got, ref):
+    """Largest rel-L2 over the instances of a batch: every axis but the last
+    indexes an instance, the last one runs along it.  A wrong instance, or a
+    wrong stretch of one, cannot hide under the norm of the others."""
+    got = np.asarray(got, dtype=np.complex128)
+    ref = np.asarray(ref, dtype=np.complex128)
+    if ref.ndim <= 1:
+        return rel_l2(got, ref)
+    g = got.reshape(-1, got.shape[-1])
+    r = ref.reshape(-1, ref.shape[-1])
+    return max(rel_l2(a, b) for a, b in zip(g, r))
+
+
 def to_dev(x, dtype):
     import torch
     npdt = np.complex64 if dtype == "f32" else np.complex128

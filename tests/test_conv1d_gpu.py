@@ -3,14 +3,15 @@
 Tolerances: FP64 on integer-valued inputs must round (rint) to the exact
 oracle result; FP64 on real-valued inputs rel-L2 <= 1e-12; FP32 rel-L2 <=
 1e-5 (the FP32 contract: FFT rounding grows like eps * log2 S, eps = 6e-8,
-and the residue sum is compensated from 8 residues on).
+and the residue sum is compensated from 8 residues on).  Norms are taken
+per instance of a batch and the largest must meet the bound.
 """
 import numpy as np
 import pytest
 
 import inputs
 from oracle import cdirect, direct, params, residue
-from tests.gpu_util import rel_l2, run_conv, to_dev
+from tests.gpu_util import rel_l2, rel_l2_rows, run_conv, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -40,7 +41,7 @@ def check(got, ref, dtype, integer, ctx):
         assert np.max(np.abs(got - r)) < 1e-6, ctx
     else:
         tol = F32_TOL if dtype == "f32" else F64_TOL
-        e = rel_l2(got, ref)
+        e = rel_l2_rows(got, ref)
         assert e <= tol, (ctx, e)
 
 
@@ -268,7 +269,7 @@ def test_persistent_bulk_copy_variant_matches_plain_kernel(hd):
     subprocess.run([sys.executable, "-c", code], cwd=root, env=env, check=True, timeout=300)
     plains = [np.load(f"/tmp/hd_plain_{i}.npy") for i in range(len(outs))]
     for i, got in enumerate(outs):
-        assert rel_l2(got, plains[i]) <= 1e-6, i
+        assert rel_l2_rows(got, plains[i]) <= 1e-6, i
     # a misaligned row start (one complex64 past a 16-byte boundary) takes the plain kernel
     buf = [np.zeros((count * L + 1,), dtype=np.complex64) for _ in range(2)]
     for a in range(2):

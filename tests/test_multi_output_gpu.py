@@ -13,7 +13,7 @@ import pytest
 
 import inputs
 from oracle import direct, params
-from tests.gpu_util import rel_l2, to_dev
+from tests.gpu_util import rel_l2, rel_l2_rows, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -52,7 +52,7 @@ def check(got, ref, dtype, integer, ctx):
         assert np.array_equal(r, ref), ctx
     else:
         for b in range(ref.shape[0]):
-            e = rel_l2(got[b], ref[b])
+            e = rel_l2_rows(got[b], ref[b])
             assert e <= (1e-5 if dtype == "f32" else 1e-12), (ctx, b, e)
 
 

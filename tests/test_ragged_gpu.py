@@ -1,6 +1,8 @@
 """GPU parity of ragged batches (one persistent kernel launch replayed from a
 CUDA graph) against the FP64 direct oracle, plus the bounded-wait failure
 path of the persistent kernel."""
+import os
+
 import numpy as np
 import pytest
 
@@ -99,9 +101,12 @@ def test_ragged_wait_timeout_is_reported(hd):
         assert rel_l2(hs[0].cpu().numpy(), oracle_of(descs[0], host[0])) <= 1e-5
 
 
-def test_ragged_full_size_sampled(hd):
+def test_ragged_full_size(hd):
     """10,000 instances, L log-uniform on [64, 65536], L/M on [0.3, 0.67],
-    A in {2, 3}: sampled instances against the oracle."""
+    A in {2, 3}.  For every class of instances present (transform size S,
+    kind, A) the shortest instance is compared in full with the FP64 direct
+    sum; nine more instances (shortest, median, longest L) on 64 points."""
+    import concurrent.futures as cf
     import torch
     descs = inputs.ragged_instances(10000, 4)
     tot = sum(d["L"] for d in descs)
@@ -116,13 +121,38 @@ def test_ragged_full_size_sampled(hd):
         plan.bind(fs, hs)
         plan.run()
         assert plan.status() == "HD_OK"
-        order = np.argsort([d["L"] for d in descs])
-        pick = list(order[:3]) + list(order[len(order) // 2: len(order) // 2 + 3]) + list(order[-3:])
-        for i in pick:
-            d = descs[i]
-            xs = [f.cpu().numpy() for f in fs[i]]
-            idx = np.unique(np.linspace(0, d["L"] - 1, 64).astype(np.int64))
-            mult = "product" if d["A"] == 2 else "sum_pairs3"
-            want = cdirect.conv1d_points([x.astype(np.complex128) for x in xs], d["L"], idx, d["kind"], mult)
-            got = hs[i].cpu().numpy()[idx]
-            assert rel_l2(got, want) <= 1e-5, (i, d, plan.params(i))
+        params = [plan.params(i) for i in range(len(descs))]
+    got_all = out.cpu().numpy()
+    offs = np.concatenate([[0], np.cumsum([d["L"] for d in descs])])
+    host = [x.cpu().numpy() for x in base]
+    classes = {}
+    for i, d in enumerate(descs):
+        key = (params[i]["S"], d["kind"], d["A"])
+        if key not in classes or d["L"] < descs[classes[key]]["L"]:
+            classes[key] = i
+    split_sizes = {k[0] for k in classes if k[0] > 4096}
+    assert len(split_sizes) >= 3 and split_sizes <= {8192, 16384, 32768, 65536}, sorted(split_sizes)
+    assert {(k[1], k[2]) for k in classes if k[0] > 4096} == {("complex", 2), ("complex", 3),
+                                                              ("centered", 2), ("centered", 3)}
+
+    def full_check(i):
+        d = descs[i]
+        xs = [host[a][offs[i]:offs[i + 1]][None, :].astype(np.complex128) for a in range(d["A"])]
+        mult = "product" if d["A"] == 2 else "sum_pairs3"
+        want = cdirect.conv1d_batch(xs, d["L"], d["kind"], mult, nthreads=1)[0]
+        return i, rel_l2(got_all[offs[i]:offs[i + 1]], want)
+
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        errs = dict(ex.map(full_check, sorted(classes.values(), key=lambda i: -descs[i]["L"])))
+    bad = {i: (descs[i], params[i], e) for i, e in errs.items() if not e <= 1e-5}
+    assert not bad, bad
+    order = np.argsort([d["L"] for d in descs])
+    pick = list(order[:3]) + list(order[len(order) // 2: len(order) // 2 + 3]) + list(order[-3:])
+    for i in pick:
+        d = descs[i]
+        xs = [host[a][offs[i]:offs[i + 1]] for a in range(d["A"])]
+        idx = np.unique(np.linspace(0, d["L"] - 1, 64).astype(np.int64))
+        mult = "product" if d["A"] == 2 else "sum_pairs3"
+        want = cdirect.conv1d_points([x.astype(np.complex128) for x in xs], d["L"], idx, d["kind"], mult)
+        got = got_all[offs[i]:offs[i + 1]][idx]
+        assert rel_l2(got, want) <= 1e-5, (i, d, params[i])

@@ -6,7 +6,7 @@ import pytest
 
 import inputs
 from oracle import cdirect, params
-from tests.gpu_util import rel_l2, run_conv
+from tests.gpu_util import rel_l2_rows, run_conv
 from tests.test_conv1d_gpu import check, make_inputs
 
 pytestmark = pytest.mark.gpu
@@ -38,7 +38,7 @@ def test_split_f32_matches_oracle(hd, kind, L, A):
         with hd.Plan(L, M, A=A, kind=kind, candidate=c) as plan:
             assert plan.params()["scratch_bytes"] > 0
             got = run_conv(hd, plan, fs)
-            e = rel_l2(got, ref)
+            e = rel_l2_rows(got, ref)
             assert e <= 1e-5, (c, e)
 
 
@@ -68,4 +68,4 @@ def test_split_chunking_and_inplace(hd):
         plan.convolve_batched(d, d[0], count, L)
         torch.cuda.synchronize()
         got = d[0].cpu().numpy()[ref_idx]
-        assert rel_l2(got, ref) <= 1e-5
+        assert rel_l2_rows(got, ref) <= 1e-5

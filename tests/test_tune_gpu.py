@@ -3,7 +3,7 @@ import numpy as np
 import pytest
 
 from oracle import direct, params
-from tests.gpu_util import rel_l2, run_conv
+from tests.gpu_util import rel_l2_rows, run_conv
 from tests.test_conv1d_gpu import check, make_inputs
 
 pytestmark = pytest.mark.gpu
@@ -39,7 +39,7 @@ def test_sum_pairs3_variants(hd):
     for c in hd.enumerate_candidates(L=L, M=M, A=3):
         with hd.Plan(L, M, A=3, candidate=c) as plan:
             got = run_conv(hd, plan, fs)
-            assert rel_l2(got, ref) <= 1e-5, c
+            assert rel_l2_rows(got, ref) <= 1e-5, c
 
 
 def test_autotune_populates_cache_and_plans_use_it(hd):
@@ -56,6 +56,6 @@ def test_autotune_populates_cache_and_plans_use_it(hd):
         assert (p["m"], p["p"], p["q"]) == (best["m"], best["p"], best["q"])
         fs = make_inputs("centered", 2048, 2, 3, 77)
         got = run_conv(hd, plan, fs)
-        assert rel_l2(got, direct.conv1d_batch(fs, "centered")) <= 1e-5
+        assert rel_l2_rows(got, direct.conv1d_batch(fs, "centered")) <= 1e-5
     hd.tune_cache_clear()
     assert hd.tune_cache_get(**kw) is None
