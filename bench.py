@@ -1,7 +1,8 @@
 """Benchmark of the hybrid-dealiased convolution path on GB300.
 
-Workloads (``--workload``):
-  batch1d   (default) 4096 independent 1D complex convolutions, A = 2, B = 1,
+Workloads (``--workload``; the default, ``all``, prints the 1D batch as the
+headline line and every other workload under ``workloads``, in one run):
+  batch1d   4096 independent 1D complex convolutions, A = 2, B = 1,
             L = 4096, complex64, once with the centered 2/3 padding
             M = ceil(3L/2) = 6144 and once with the 1/2 padding M = 2L-1 = 8191:
             two hd_convolve_batched calls, 8192 convolutions per step.
@@ -345,13 +346,36 @@ def roofline(bytes_launch, ms_launch, traffic=None, kernel=""):
             "bytes_per_launch": bytes_launch, "ms_per_launch": ms_launch, "kernel": kernel}
 
 
-def alu(flops_launch, ms_launch, clocks):
+ALU_PEAKS = {}
+
+
+def measure_alu_peaks(hd):
+    """FP32 and FP64 FMA peaks of this GPU, measured by the library's own
+    microbenchmark (hd_alu_peak): the best of scalar and packed FP32 FMAs, and
+    FP64 FMAs.  Taken once per run, before the workloads."""
+    if not ALU_PEAKS:
+        f32, f32x2 = hd.alu_peak("f32"), hd.alu_peak("f32x2")
+        ALU_PEAKS.update({"f32_tflops": max(f32, f32x2), "f32_scalar_fma_tflops": f32, "f32x2_fma_tflops": f32x2,
+                          "f64_tflops": hd.alu_peak("f64"),
+                          "how": "hd_alu_peak: 8 chains of dependent FMAs per thread, 8 CTAs x 256 threads per SM, "
+                                 "CUDA events over 5 launches"})
+    return ALU_PEAKS
+
+
+def alu(flops_launch, ms_launch, clocks, dtype="f32"):
+    """FFT flop rate of the dominant kernel against the measured FMA peak of its
+    precision (nominal spec figure for context)."""
     mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
-    peak = SM_COUNT * FP32_LANES * 2 * mhz * 1e6 / 1e12
+    nominal = SM_COUNT * FP32_LANES * 2 * mhz * 1e6 / 1e12
+    peak = ALU_PEAKS.get(f"{dtype}_tflops")
     ach = flops_launch / (ms_launch * 1e-3) / 1e12
-    return {"achieved_tflops": ach, "peak_tflops": peak, "frac": ach / peak, "flops_per_launch": flops_launch,
-            "convention": "5 S log2 S per complex FFT of size S, (A+B) n transforms per convolution",
-            "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES} FP32 lanes x 2 (FMA) x {mhz:.0f} MHz (sampled)"}
+    out = {"achieved_tflops": ach, "peak_tflops": peak, "frac": ach / peak if peak else None,
+           "flops_per_launch": flops_launch, "peak_source": "measured (hd_alu_peak, this run)" if peak else None,
+           "convention": "5 S log2 S per complex FFT of size S, (A+B) n transforms per convolution"}
+    if dtype == "f32":
+        out["nominal_peak_tflops"] = nominal
+        out["nominal_basis"] = f"{SM_COUNT} SMs x {FP32_LANES} FP32 lanes x 2 (FMA) x {mhz:.0f} MHz (sampled)"
+    return out
 
 
 _CODE_TOKENS = re.compile(r'("(?:\\.|[^"\\\n])*")|//[^\n]*|/\*.*?\*/', re.S)
@@ -495,6 +519,7 @@ def run_batch1d(args, ctx, hd):
 
     e2e_ms = ctx.max_over_ranks(ctx.time_it(e2e_step, max(3, min(args.steps, 10))))
     e2e_ok = all(torch.equal(h_out[si], hout[si].cpu()) for si in range(len(SUBS)))
+    link = host_link(ctx, [x for row in h_in for x in row], [x for row in d_in for x in row], h_out, d_out)
     for row in splans:
         for p_ in row:
             p_.close()
@@ -539,8 +564,10 @@ def run_batch1d(args, ctx, hd):
                 ref = cdirect.conv1d_batch(fs, L1D, kind)
                 got = f64out[si][samp].cpu().numpy()
                 err[kind] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+            f64_flops = sum(COUNT * conv_flops(p64[i].axis_params(0)["S"], p64[i].axis_params(0)["n"])
+                            for i in range(len(SUBS)))
             baselines[name] = {"value": COUNT * len(SUBS) / (t64 * 1e-3), "unit": "conv/s", "ms_per_step": t64,
-                               "rel_l2": err,
+                               "alu": alu(f64_flops, t64, {}, "f64"), "rel_l2": err,
                                "params": {SUBS[i][0]: p64[i].axis_params(0) for i in range(len(SUBS))}}
             for p in p64:
                 p.close()
@@ -563,7 +590,8 @@ def run_batch1d(args, ctx, hd):
         "e2e": {"value": convs_step / (e2e_ms * 1e-3), "unit": "conv/s",
                 "h2d_bytes_per_step": len(SUBS) * 2 * COUNT * L1D * 8,
                 "d2h_bytes_per_step": len(SUBS) * COUNT * L1D * 8, "ms_per_step": e2e_ms,
-                "pipelining": f"{NCH} chunks per sub-config over {NS} streams", "outputs_match_device_run": e2e_ok},
+                "pipelining": f"{NCH} chunks per sub-config over {NS} streams", "outputs_match_device_run": e2e_ok,
+                "host_link": link},
         "gpu_launches": args.steps * len(SUBS),
         "clocks": clocks,
         "accuracy": acc,
@@ -575,9 +603,9 @@ def run_batch1d(args, ctx, hd):
         rate_x, sample_x = oracle_rate_explicit_1d(3.0, L1D, SUBS)
         out["baselines"]["cpu_fp64_explicit_fft"] = {"value": rate_x, "unit": "conv/s", "cores": 1,
                                                      "sample": sample_x}
-    emit(ctx, out)
     for p in plans:
         p.close()
+    return out
 
 
 # ----------------------------------------------------------------------------- single64
@@ -614,6 +642,7 @@ def run_single64(args, ctx, hd):
                      "params": {k: best[k] for k in ("m", "p", "q", "S", "n", "E", "minb", "ms")},
                      "candidates": [{k: c[k] for k in ("m", "p", "q", "S", "n", "ms")} for c in allc]})
     out.update({"roofline": roofline(3 * L * 16, ms1, None, "conv1d_kernel f64 (latency-bound single convolution)"),
+                "alu": alu(conv_flops(best["S"], best["n"]), ms1, clocks, "f64"),
                 "accuracy": {"exact_after_rint": bool(np.array_equal(r, ref)),
                              "max_dev_from_integer": float(np.max(np.abs(got - r)))},
                 "gpu_launches": K * reps, "clocks": clocks,
@@ -621,8 +650,39 @@ def run_single64(args, ctx, hd):
     if ctx.rank == 0 and not args.no_cpu_baseline:
         rate, nt, sample = oracle_rate_1d(10.0, L, ["complex"], integer=True)
         out["cpu_baseline"] = {"value": rate, "unit": "conv/s", "cores": nt, "kind": "oracle", "sample": sample}
-    emit(ctx, out)
     plan.close()
+    return out
+
+
+def host_link(ctx, h_src, d_dst, h_dst, d_src, reps=5):
+    """Plain copies between pinned host memory and the device with the byte
+    counts of one end-to-end step: host->device alone, device->host alone, and
+    both at once on two streams (GB/s).  The ceiling of the e2e figure."""
+    torch = ctx.torch
+    up = sum(x.numel() * x.element_size() for x in h_src)
+    down = sum(x.numel() * x.element_size() for x in h_dst)
+
+    def h2d():
+        for a, b in zip(d_dst, h_src):
+            a.copy_(b, non_blocking=True)
+
+    def d2h():
+        for a, b in zip(h_dst, d_src):
+            a.copy_(b, non_blocking=True)
+    s2 = torch.cuda.Stream()
+
+    def both():
+        s2.wait_stream(ctx.stream)
+        h2d()
+        with torch.cuda.stream(s2):
+            d2h()
+        ctx.stream.wait_stream(s2)
+    t_up = ctx.time_it(h2d, reps)
+    t_down = ctx.time_it(d2h, reps)
+    t_both = ctx.time_it(both, reps)
+    return {"h2d_gbs": up / (t_up * 1e-3) / 1e9, "d2h_gbs": down / (t_down * 1e-3) / 1e9,
+            "both_gbs": (up + down) / (t_both * 1e-3) / 1e9, "h2d_bytes": up, "d2h_bytes": down,
+            "ms_h2d": t_up, "ms_d2h": t_down, "ms_both": t_both}
 
 
 def e2e_single(ctx, plan, fs, L):
@@ -701,7 +761,7 @@ def run_2d(args, ctx, hd):
     if ctx.rank == 0 and not args.no_cpu_baseline:
         rate, nt, sample = oracle_rate_nd("2d")
         out["cpu_baseline"] = {"value": rate, "unit": "conv/s", "cores": nt, "kind": "oracle", "sample": sample}
-    emit(ctx, out)
+    return out
 
 
 def e2e_nd(ctx, plan, f, hh):
@@ -796,7 +856,7 @@ def run_ns2d(args, ctx, hd):
     if ctx.rank == 0 and not args.no_cpu_baseline:
         rate, nt, sample = oracle_rate_nd("ns2d")
         out["cpu_baseline"] = {"value": rate, "unit": "conv/s", "cores": nt, "kind": "oracle", "sample": sample}
-    emit(ctx, out)
+    return out
 
 
 # ----------------------------------------------------------------------------- 3d
@@ -882,7 +942,7 @@ def run_3d(args, ctx, hd):
         rate, nt, sample = oracle_rate_nd("3d")
         out["cpu_baseline"] = {"value": rate, "unit": "conv/s", "cores": nt, "kind": "oracle", "sample": sample}
     plan.close()
-    emit(ctx, out)
+    return out
 
 
 # ----------------------------------------------------------------------------- ragged
@@ -990,7 +1050,7 @@ def run_ragged(args, ctx, hd):
     if ctx.rank == 0 and not args.no_cpu_baseline:
         rate, nt, sample = oracle_rate_ragged(10.0, descs)
         out["cpu_baseline"] = {"value": rate, "unit": "conv/s", "cores": nt, "kind": "oracle", "sample": sample}
-    emit(ctx, out)
+    return out
 
 
 def main():
@@ -999,7 +1059,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="hd", choices=["hd", "reference"])
-    ap.add_argument("--workload", default="batch1d", choices=list(WORKLOAD_NAMES))
+    ap.add_argument("--workload", default="all", choices=["all"] + list(WORKLOAD_NAMES),
+                    help="all (default): the 1D batch as the headline line, every other workload under `workloads`")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="batch1d: skip the FP64 baselines")
     ap.add_argument("--m", type=str, default="auto", help="batch1d: m per sub-config, e.g. 2048,4096")
@@ -1009,17 +1070,45 @@ def main():
     ap.add_argument("--e2e-chunks", type=int, default=8, help="batch1d e2e: chunks per sub-config")
     ap.add_argument("--train-steps", type=int, default=2000)
     ap.add_argument("--exhaustive", action="store_true", help="ragged: also time the per-instance exhaustive search")
+    ap.add_argument("--no-exhaustive", action="store_true",
+                    help="all: skip the ragged per-instance exhaustive search (on by default there)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
+        if args.workload == "all":
+            args.workload = "batch1d"
         run_reference(args)
         return
     import __graft_entry__
     __graft_entry__.build()
     import paper_2303_17510_gb300 as hd
     ctx = Ctx()
-    {"batch1d": run_batch1d, "single64": run_single64, "2d": run_2d, "ragged": run_ragged,
-     "3d": run_3d, "ns2d": run_ns2d}[args.workload](args, ctx, hd)
+    runs = {"batch1d": run_batch1d, "single64": run_single64, "2d": run_2d, "ragged": run_ragged,
+            "3d": run_3d, "ns2d": run_ns2d}
+    peaks_ = measure_alu_peaks(hd)
+    if args.workload != "all":
+        out = runs[args.workload](args, ctx, hd)
+        out["alu_peaks"] = peaks_
+        emit(ctx, out)
+    else:
+        # the 1D batch is the headline line; every other workload runs after it in the same
+        # process, under one clock record (`clocks_all`), and is reported under `workloads`
+        clk_all = ClockSampler(ctx.local).start()
+        t_all = time.perf_counter()
+        out = run_batch1d(args, ctx, hd)
+        args.exhaustive = not args.no_exhaustive
+        wl = {}
+        for name in ("single64", "2d", "3d", "ragged", "ns2d"):
+            t0 = time.perf_counter()
+            o = runs[name](args, ctx, hd)
+            for k in ("metric", "n_gpus", "steps", "warmup", "higher_is_better", "scaling", "vs_baseline"):
+                o.pop(k, None)
+            o["wall_s"] = time.perf_counter() - t0
+            wl[name] = o
+        out["workloads"] = wl
+        out["alu_peaks"] = peaks_
+        out["clocks_all"] = dict(clk_all.stop(), wall_s=time.perf_counter() - t_all)
+        emit(ctx, out)
     if ctx.dist is not None:
         ctx.dist.destroy_process_group()
 

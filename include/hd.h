@@ -87,7 +87,9 @@ typedef struct hd_plan hd_plan;
  * all residues of an axis in one block.  Fewer residues per block (D[i] < n)
  * are allowed on the outermost axis only (a middle axis of a 3D plan writes
  * its outputs over its inputs, so it reads all of them first);
- * HD_ERR_UNSUPPORTED otherwise. */
+ * HD_ERR_UNSUPPORTED otherwise.  flags: 0, or HD_PLAN_NO_WORK_BUFFER (below);
+ * unknown bits are HD_ERR_INVALID.  Zero-initialize the struct (memset or
+ * = {0}) so that fields added at its end later read as 0. */
 typedef struct {
     int ndim;
     int64_t L[3];
@@ -102,7 +104,15 @@ typedef struct {
     int64_t q[3];
     int D[3];
     int64_t row_pitch[3];
+    int flags;
 } hd_desc;
+
+/* Plan flag, 1D plans only (N-D plans return HD_ERR_UNSUPPORTED): a plan whose
+ * residue transforms take the split path allocates no work buffer of its own.
+ * Only hd_convolve_batched_noalloc runs such a plan (hd_convolve and
+ * hd_convolve_batched return HD_ERR_UNSUPPORTED on it); on the fused path the
+ * flag changes nothing, since no work buffer is needed there. */
+enum { HD_PLAN_NO_WORK_BUFFER = 1 };
 
 /* Derive (p, q, n) from (kind, L, M, m): Eq. pqdef1 with Alg. convolve
  * (complex: p = ceil(L/m); p <= 2: q = n = ceil(M/m); p > 2: n =
@@ -336,8 +346,13 @@ hd_status hd_ragged_inject_stall(hd_plan* plan, int64_t i);
  *     needs clearing, but calls whose kernels overlap on the GPU (different
  *     streams, or several host threads) race on the buffer: order them on one
  *     stream or synchronize between them.
- *   - Plans that use no work buffer (the fused path) return HD_ERR_UNSUPPORTED.
- * Arguments and results are those of hd_convolve_batched. */
+ *   - Plans that use no work buffer (the fused path) return HD_ERR_UNSUPPORTED;
+ *     ragged and N-D plans return HD_ERR_INVALID.
+ *   - A plan created with the flag HD_PLAN_NO_WORK_BUFFER skips the plan's own
+ *     work buffer, so nothing but its twiddle tables is allocated for it.
+ *   - Like hd_convolve_batched, the call makes the plan's device current for
+ *     its duration (and restores the caller's device).
+ * Arguments and results are otherwise those of hd_convolve_batched. */
 #define HD_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
 hd_status hd_convolve_batched_noalloc(const hd_plan* plan, int64_t count, const void* const* f, void* const* h,
                                       int64_t batch_stride, void* stream);
@@ -350,6 +365,17 @@ hd_status hd_convolve_batched_noalloc(const hd_plan* plan, int64_t count, const 
  * inputs with asynchronous bulk copies whose completion they wait for with a
  * time limit.) */
 hd_status hd_device_status(void);
+
+/* Arithmetic peak of the current device (no counterpart in the paper; the
+ * roofline of the FFT kernels, which run on the CUDA cores): FMA throughput in
+ * TFLOP/s (2 flops per FMA lane) measured by the library's own kernels, many
+ * CTAs per SM each running independent chains of dependent FMAs, timed with
+ * CUDA events over 5 launches after one warm-up launch.  kind: HD_PEAK_F32
+ * (scalar FP32 FMA), HD_PEAK_F64 (FP64 FMA) or HD_PEAK_F32X2 (the packed
+ * two-lane FP32 FMA of sm_100 and later).  Synchronizes the device; allocates
+ * and frees a small output buffer. */
+enum { HD_PEAK_F32 = 0, HD_PEAK_F64 = 1, HD_PEAK_F32X2 = 2 };
+hd_status hd_alu_peak(int kind, double* tflops);
 
 /* Releases the plan's device memory (after synchronizing its device). NULL ok. */
 hd_status hd_plan_destroy(hd_plan* plan);

@@ -25,6 +25,7 @@ lib = ctypes.CDLL(LIB_PATH)
 KIND = {"complex": 0, "centered": 1, "hermitian": 2}
 DTYPE = {"f32": 0, "f64": 1}
 MULT = {"product": 0, "sum_pairs3": 1, "basdevant2": 2}
+PLAN_NO_WORK_BUFFER = 1   # HD_PLAN_NO_WORK_BUFFER
 MULT_AB = {"product": (2, 1), "sum_pairs3": (3, 1), "basdevant2": (2, 2)}   # inputs A, outputs B
 
 
@@ -45,7 +46,8 @@ _vp = ctypes.c_void_p
 class hd_desc(ctypes.Structure):
     _fields_ = [("ndim", ctypes.c_int), ("L", _i64 * 3), ("M", _i64 * 3), ("A", ctypes.c_int), ("B", ctypes.c_int),
                 ("kind", ctypes.c_int), ("dtype", ctypes.c_int), ("mult", ctypes.c_int), ("m", _i64 * 3),
-                ("p", _i64 * 3), ("q", _i64 * 3), ("D", ctypes.c_int * 3), ("row_pitch", _i64 * 3)]
+                ("p", _i64 * 3), ("q", _i64 * 3), ("D", ctypes.c_int * 3), ("row_pitch", _i64 * 3),
+                ("flags", ctypes.c_int)]
 
 
 class hd_candidate(ctypes.Structure):
@@ -96,6 +98,7 @@ _sig("hd_plan_create_candidate", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POIN
 _sig("hd_tune_cache_put", ctypes.c_int, [ctypes.POINTER(hd_desc), ctypes.POINTER(hd_candidate)])
 _sig("hd_tune_cache_get", ctypes.c_int, [ctypes.POINTER(hd_desc), ctypes.POINTER(hd_candidate)])
 _sig("hd_tune_cache_clear", ctypes.c_int, [])
+_sig("hd_alu_peak", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)])
 _sig("hd_convolve_batched_noalloc", ctypes.c_int, [_vp, _i64, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i64, _vp])
 _sig("hd_mlp_create", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int)])
 _sig("hd_mlp_num_params", _i64, [_vp])
@@ -135,6 +138,17 @@ def device_status() -> str:
     return STATUS[lib.hd_device_status()]
 
 
+PEAK_KINDS = {"f32": 0, "f64": 1, "f32x2": 2}
+
+
+def alu_peak(kind="f32") -> float:
+    """Measured FMA throughput of the current device in TFLOP/s: "f32" (scalar
+    FP32 FMA), "f64" or "f32x2" (packed two-lane FP32 FMA)."""
+    v = ctypes.c_double()
+    _check(lib.hd_alu_peak(PEAK_KINDS[kind], ctypes.byref(v)), "hd_alu_peak")
+    return v.value
+
+
 def status_string(code: int) -> str:
     return lib.hd_status_string(int(code)).decode()
 
@@ -165,7 +179,7 @@ def _stream(stream) -> int:
     return int(stream.cuda_stream)
 
 
-def make_desc(L, M, A=2, B=None, m=0, p=0, q=0, D=0, kind="complex", dtype="f32", mult=None, ndim=None):
+def make_desc(L, M, A=2, B=None, m=0, p=0, q=0, D=0, kind="complex", dtype="f32", mult=None, ndim=None, flags=0):
     mult, A, B = _mult_of(A, B, mult)
     Ls = list(L) if isinstance(L, (list, tuple)) else [L]
     Ms = list(M) if isinstance(M, (list, tuple)) else [M]
@@ -179,6 +193,7 @@ def make_desc(L, M, A=2, B=None, m=0, p=0, q=0, D=0, kind="complex", dtype="f32"
     for i in range(nd):
         d.L[i], d.M[i], d.m[i], d.p[i], d.q[i], d.D[i] = Ls[i], Ms[i], ms[i], ps[i], qs[i], Ds[i]
     d.A, d.B, d.kind, d.dtype, d.mult = A, B, KIND[kind], DTYPE[dtype], MULT[mult]
+    d.flags = int(flags)
     return d
 
 
@@ -226,9 +241,11 @@ class Plan:
     """A convolution plan (owns device twiddle tables and scratch)."""
 
     def __init__(self, L, M, A=2, B=None, m=0, p=0, q=0, D=0, kind="complex", dtype="f32", mult=None, ndim=None,
-                 candidate=None):
+                 candidate=None, flags=0):
+        """flags: 0, or PLAN_NO_WORK_BUFFER (a 1D split-path plan without its own
+        work buffer, for convolve_batched_noalloc only)."""
         mult, A, B = _mult_of(A, B, mult)
-        d = make_desc(L, M, A, B, m, p, q, D, kind, dtype, mult, ndim)
+        d = make_desc(L, M, A, B, m, p, q, D, kind, dtype, mult, ndim, flags)
         self._h = _vp()
         if candidate is None:
             _check(lib.hd_plan_create_ex(ctypes.byref(self._h), ctypes.byref(d)), "hd_plan_create_ex")
@@ -318,6 +335,10 @@ class RaggedPlan:
             _check(lib.hd_ragged_create_candidates(ctypes.byref(self._h), n, arr, ca), "hd_ragged_create_candidates")
         self.n = n
         self.descs = descs
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
 
     def bind(self, fs, hs):
         """fs[i]: list of A device arrays of instance i; hs[i]: its output."""

@@ -131,6 +131,8 @@ hd_status plan_create_nd(hd_plan** out, const hd_desc* d) {
     if (d->kind < HD_COMPLEX || d->kind > HD_HERMITIAN) return HD_ERR_INVALID;
     if (d->dtype != HD_F32 && d->dtype != HD_F64) return HD_ERR_INVALID;
     if (!mult_counts_ok(d->mult, d->A, d->B)) return HD_ERR_INVALID;
+    if (d->flags & ~HD_PLAN_NO_WORK_BUFFER) return HD_ERR_INVALID;
+    if (d->flags) return HD_ERR_UNSUPPORTED;
     for (int i = 0; i < nd; ++i) {
         if (d->L[i] <= 0 || d->M[i] <= 0 || d->m[i] < 0 || d->p[i] < 0 || d->q[i] < 0 || d->D[i] < 0)
             return HD_ERR_INVALID;

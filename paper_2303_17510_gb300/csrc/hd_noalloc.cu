@@ -17,7 +17,8 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_addr[kMaxDevices];
 
-// Device address of g_noalloc_work on the current device (looked up once per device).
+// Device address of g_noalloc_work on device `dev`, which must be current
+// (looked up once per device).
 hd_status work_address(int dev, void** out) {
     if (dev < 0 || dev >= kMaxDevices) return HD_ERR_UNSUPPORTED;
     std::lock_guard<std::mutex> g(g_mu);
@@ -38,8 +39,8 @@ hd_status work_address(int dev, void** out) {
 extern "C" hd_status hd_convolve_batched_noalloc(const hd_plan* plan, int64_t count, const void* const* f,
                                                   void* const* h, int64_t batch_stride, void* stream) {
     if (!plan || !f || !h || count < 0) return HD_ERR_INVALID;
+    if (plan->ragged || plan->ndim != 1) return HD_ERR_INVALID;
     if (plan->sticky != HD_OK) return plan->sticky;
-    if (plan->ndim != 1) return HD_ERR_UNSUPPORTED;
     const hd::AxisPlan& ax = plan->ax[0];
     if (ax.path != hd::PATH_SPLIT) return HD_ERR_UNSUPPORTED;
     for (int a = 0; a < plan->A; ++a)
@@ -51,12 +52,13 @@ extern "C" hd_status hd_convolve_batched_noalloc(const hd_plan* plan, int64_t co
     const size_t per = (size_t)plan->A * (size_t)ax.n * (size_t)ax.S * esz;
     if (per > HD_NOALLOC_SCRATCH_BYTES) return HD_ERR_SCRATCH_LIMIT;
     if (count == 0) return HD_OK;
+    hd::DeviceGuard guard(plan->device);   // the plan's device, as hd_convolve_batched does
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
         return HD_ERR_CUDA;
     }
-    if (dev != plan->device) return HD_ERR_INVALID;
+    if (dev != plan->device) return HD_ERR_CUDA;
     void* work = nullptr;
     hd_status st = work_address(dev, &work);
     if (st != HD_OK) return st;

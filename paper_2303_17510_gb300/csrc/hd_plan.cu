@@ -25,19 +25,6 @@ bool comp_default(int64_t n) {
 
 namespace {
 
-struct DeviceGuard {
-    int prev = -1;
-    bool changed = false;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
-            changed = cudaSetDevice(dev) == cudaSuccess;
-        }
-    }
-    ~DeviceGuard() {
-        if (changed) cudaSetDevice(prev);
-    }
-};
-
 int64_t next_pow2(int64_t x) {
     int64_t p = 1;
     while (p < x) p <<= 1;
@@ -154,6 +141,7 @@ hd_status check_desc_1d(const hd_desc* d) {
     if (!mult_counts_ok(d->mult, d->A, d->B)) return HD_ERR_INVALID;
     if (d->L[0] <= 0 || d->M[0] <= 0 || d->m[0] < 0 || d->p[0] < 0 || d->q[0] < 0) return HD_ERR_INVALID;
     if (d->M[0] < hd_dealias_bound(d->kind, d->mult, d->L[0])) return HD_ERR_ALIASED;
+    if (d->flags & ~HD_PLAN_NO_WORK_BUFFER) return HD_ERR_INVALID;
     return HD_OK;
 }
 
@@ -195,8 +183,8 @@ hd_status plan_finish(const hd_desc* d, const AxisPlan& ax, hd_plan** out) {
             if (ch > 2048) ch = 2048;
             if (ch < 1) ch = 1;
             a0.chunk = ch;
-            pl->scratch_bytes = per * (size_t)ch;
-            if (cudaMalloc(&pl->scratch, pl->scratch_bytes) != cudaSuccess) {
+            pl->scratch_bytes = (d->flags & HD_PLAN_NO_WORK_BUFFER) ? 0 : per * (size_t)ch;
+            if (pl->scratch_bytes && cudaMalloc(&pl->scratch, pl->scratch_bytes) != cudaSuccess) {
                 cudaGetLastError();
                 pl->scratch = nullptr;
                 st = HD_ERR_NOMEM;
@@ -357,6 +345,7 @@ hd_status plan_execute(hd_plan* pl, int64_t count, const void* const* f, void* c
     }
     const AxisPlan& ax = pl->ax[0];
     if (ax.path == PATH_SPLIT) {
+        if (!pl->scratch) return HD_ERR_UNSUPPORTED;   // created without a work buffer
         hd_status s2 = split_execute(*pl, ax, count, f, h, stride, pl->scratch, ax.chunk, st);
         if (s2 != HD_OK) pl->sticky = s2;
         return s2;

@@ -17,6 +17,23 @@ enum { PATH_FUSED = 0, PATH_SPLIT = 1, PATH_COLUMN = 2 };
 
 struct RaggedData;
 
+// Makes `dev` the current device for the guard's lifetime (restores the
+// caller's device afterwards).
+struct DeviceGuard {
+    int prev = -1;
+    bool changed = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
+            changed = cudaSetDevice(dev) == cudaSuccess;
+        }
+    }
+    ~DeviceGuard() {
+        if (changed) cudaSetDevice(prev);
+    }
+    DeviceGuard(const DeviceGuard&) = delete;
+    DeviceGuard& operator=(const DeviceGuard&) = delete;
+};
+
 // One axis of a plan: the paper's parameters (m, p, q, n, D) and the
 // kernel geometry they map to (transform size S = m, p m or p m / 2;
 // n residues of S values; nb folded blocks).

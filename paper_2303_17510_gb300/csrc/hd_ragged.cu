@@ -339,7 +339,7 @@ hd_status ragged_create(hd_plan** out, int64_t n, const hd_desc* descs, const hd
         const hd_desc* d = descs + i;
         if (d->ndim != 1 || d->dtype != HD_F32 || d->B != 1 || (d->kind != HD_COMPLEX && d->kind != HD_CENTERED) ||
             !((d->mult == HD_MULT_PRODUCT && d->A == 2) || (d->mult == HD_MULT_SUM_PAIRS3 && d->A == 3)) ||
-            d->L[0] <= 0 || d->M[0] <= 0) {
+            d->L[0] <= 0 || d->M[0] <= 0 || d->flags != 0) {
             st = HD_ERR_INVALID;
             break;
         }
