@@ -252,7 +252,9 @@ def run_reference(args):
     elif wl == "single64":
         rate, nt, sample = oracle_rate_1d(budget, 1024, ["complex"], integer=True)
     elif wl == "ragged":
-        rate, nt, sample = oracle_rate_ragged(budget, inputs.ragged_instances(args.ragged_n, RAGGED_SEED))
+        from oracle import params
+        rate, nt, sample = oracle_rate_ragged(budget, inputs.ragged_instances(args.ragged_n, RAGGED_SEED,
+                                                                              params.dealias_bound))
     else:
         rate, nt, sample = oracle_rate_nd(wl)
     cfg = {"workload": WORKLOAD_NAMES[wl]}
@@ -951,7 +953,7 @@ def run_ragged(args, ctx, hd):
     from oracle import cdirect
     from paper_2303_17510_gb300 import selector
     torch = ctx.torch
-    descs = inputs.ragged_instances(args.ragged_n, RAGGED_SEED)
+    descs = inputs.ragged_instances(args.ragged_n, RAGGED_SEED, hd.dealias_bound)
     tot = sum(d["L"] for d in descs)
     base = [torch.from_numpy(inputs.uniform_complex(tot, rank_seed(ctx.rank, 5, a), dtype=np.complex64)).to(ctx.dev)
             for a in range(3)]

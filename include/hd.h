@@ -71,8 +71,15 @@ enum { HD_F32 = 0, HD_F64 = 1 };
  * u^2 - v^2 of its nonlinear term in Basdevant's form (Section 9 counts
  * A = B = 2).  Binary bound; 1D plans (fused kernel, S up to 4096 FP32 /
  * 2048 FP64; FP32 from S = 512 on unless a candidate of hd_enumerate_candidates
- * is given) and 2D/3D plans. */
-enum { HD_MULT_PRODUCT = 0, HD_MULT_SUM_PAIRS3 = 1, HD_MULT_BASDEVANT2 = 2 };
+ * is given) and 2D/3D plans.
+ * HD_MULT_BASDEVANT3: A = 3, B = 5, (F1 F2, F2 F3, F3 F1, F1^2 - F3^2,
+ * F2^2 - F3^2): from the velocity components u, v, w of a 3D incompressible
+ * flow, the products u v, v w, w u, u^2 - w^2 and v^2 - w^2 of its nonlinear
+ * term in Basdevant's form (Section 9 counts A = 3, B = 5).  Binary bound; 1D
+ * plans (fused kernel: the five residue sums live in shared memory, so FP32
+ * transforms up to S = 1024 and FP64 up to 512 for short rows) and 2D/3D
+ * plans; no split path. */
+enum { HD_MULT_PRODUCT = 0, HD_MULT_SUM_PAIRS3 = 1, HD_MULT_BASDEVANT2 = 2, HD_MULT_BASDEVANT3 = 3 };
 
 typedef struct hd_plan hd_plan;
 
@@ -83,11 +90,19 @@ typedef struct hd_plan hd_plan;
  * HD_CENTERED otherwise (Section 5, Hermitian data: centered outer axes,
  * Hermitian innermost axis).  m[i] = 0 selects parameters automatically;
  * p[i], q[i] = 0 derive them from m (Eq. pqdef1, Alg. convolve/convolveX,
- * Section 6.1-6.2).  D[i] = 0 selects the residue grouping automatically:
- * all residues of an axis in one block.  Fewer residues per block (D[i] < n)
- * are allowed on the outermost axis only (a middle axis of a 3D plan writes
- * its outputs over its inputs, so it reads all of them first);
- * HD_ERR_UNSUPPORTED otherwise.  flags: 0, or HD_PLAN_NO_WORK_BUFFER (below);
+ * Section 6.1-6.2).  D[i], residues per pass (Section 6.5): 0 selects the
+ * grouping automatically.  On the outer axes of N-D plans all residues of an
+ * axis run in one block by default; fewer residues per block (D[i] < n) are
+ * allowed on the outermost axis only (a middle axis of a 3D plan writes its
+ * outputs over its inputs, so it reads all of them first).  On a 1D axis
+ * whose residue transforms fit one CTA (complex or centered data), D > 1 runs
+ * D residues at once on a thread-block cluster of D * A CTAs (for few
+ * convolutions; D <= n, D * A <= 8).  On a 1D axis on the split path (larger
+ * transforms), 1 < D < n processes the residues in blocks of D, whose
+ * contributions are added into the output, so the work buffer holds A * D * S
+ * values per instance instead of A * n * S; such plans cannot write over
+ * their inputs (HD_ERR_INVALID at the call).  HD_ERR_UNSUPPORTED for a D the
+ * axis cannot take.  flags: 0, or HD_PLAN_NO_WORK_BUFFER (below);
  * unknown bits are HD_ERR_INVALID.  Zero-initialize the struct (memset or
  * = {0}) so that fields added at its end later read as 0. */
 typedef struct {
@@ -130,11 +145,11 @@ hd_status hd_derive_params(int kind, int64_t L, int64_t M, int64_t m, int64_t* p
 int64_t hd_dealias_bound(int kind, int mult, int64_t L);
 
 /* 1D complex FP32 plan.  (A, B) = (2, 1) selects HD_MULT_PRODUCT, (3, 1)
- * HD_MULT_SUM_PAIRS3, (2, 2) HD_MULT_BASDEVANT2; other (A, B) are
+ * HD_MULT_SUM_PAIRS3, (2, 2) HD_MULT_BASDEVANT2, (3, 5) HD_MULT_BASDEVANT3; other (A, B) are
  * HD_ERR_INVALID.  m = 0 selects parameters automatically
  * (tuned cache, learned selector, else a cost model); nonzero m, p, q are
  * validated: p m >= L, q m >= M, and p > 2 requires q % p == 0 (complex).
- * An explicit plan (p = q = 1, m >= M) is always legal.  D = 0 or 1.
+ * An explicit plan (p = q = 1, m >= M) is always legal.  D as in hd_desc.
  * *out receives the plan or NULL on error. */
 hd_status hd_plan_create(hd_plan** out, int64_t L, int64_t M, int A, int B, int64_t m, int64_t p, int64_t q,
                          int D);

@@ -151,7 +151,7 @@ def hermitian_3d(L: int, seed: int, alpha: float = 5.0 / 3.0, dtype=np.complex64
     return out
 
 
-def ragged_instances(count: int, seed: int, L_lo: int = 64, L_hi: int = 65536,
+def ragged_instances(count: int, seed: int, bound, L_lo: int = 64, L_hi: int = 65536,
                      ratio_lo: float = 0.3, ratio_hi: float = 0.67):
     """Workload list for a ragged batch of 1D convolutions.
 
@@ -159,9 +159,10 @@ def ragged_instances(count: int, seed: int, L_lo: int = 64, L_hi: int = 65536,
     [ratio_lo, ratio_hi]; A is 2 or 3 with probability 1/2 each; B = 1.
     Ratios above 1/2 cannot dealias the full complex product, so those
     instances use the centered kind; M is then raised, if needed, to the
-    smallest dealiased length of the kind (2L-1 complex, L + L//2 centered).
-    Returns a list of dicts with keys L, M, A, B, kind ("complex"/"centered"),
-    ratio and clamped (True when M was raised).
+    smallest dealiased length of the kind, which the caller's
+    ``bound(kind, L, mult)`` gives (this module holds no dealiasing
+    arithmetic).  Returns a list of dicts with keys L, M, A, B, kind
+    ("complex"/"centered"), ratio and clamped (True when M was raised).
     """
     g = _rng(seed)
     Ls = np.floor(np.exp(g.uniform(math.log(L_lo), math.log(L_hi), size=count))).astype(np.int64)
@@ -171,7 +172,6 @@ def ragged_instances(count: int, seed: int, L_lo: int = 64, L_hi: int = 65536,
     for L, r, A in zip(Ls.tolist(), ratios.tolist(), As.tolist()):
         kind = "centered" if r > 0.5 else "complex"
         M0 = int(math.ceil(L / r))
-        lo = (2 * L - 1) if kind == "complex" else (L + L // 2)
-        M = max(M0, lo)
+        M = max(M0, int(bound(kind, int(L), "product" if A == 2 else "sum_pairs3")))
         out.append(dict(L=int(L), M=int(M), A=int(A), B=1, kind=kind, ratio=float(r), clamped=M != M0))
     return out

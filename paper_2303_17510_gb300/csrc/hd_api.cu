@@ -142,7 +142,7 @@ int64_t split_rows(int dtype) { return max_fused_S(dtype); }
 bool split_supported(int dtype, int kind, int mult, int64_t S, int nb) {
     (void)kind;
     (void)nb;
-    if (mult == HD_MULT_BASDEVANT2) return false;   // the split row kernels have one output
+    if (mult == HD_MULT_BASDEVANT2 || mult == HD_MULT_BASDEVANT3) return false;   // the split row kernels have one output
     const int64_t S2 = split_rows(dtype);
     if (!is_pow2(S) || S <= max_fused_S(dtype)) return false;
     const int64_t S1 = S / S2;
@@ -206,7 +206,7 @@ hd_status validate_axis(int kind, int mult, int64_t L, int64_t M, int64_t m, int
 // Two CTAs per SM (128 registers) for FP32 transforms up to 2048; the
 // two-output mult holds twice the residue sums and keeps 255 registers.
 int default_minb(int dtype, int64_t S, int mult) {
-    return (dtype == HD_F32 && S <= 2048 && mult != HD_MULT_BASDEVANT2) ? 2 : 1;
+    return (dtype == HD_F32 && S <= 2048 && mult != HD_MULT_BASDEVANT2 && mult != HD_MULT_BASDEVANT3) ? 2 : 1;
 }
 
 bool fused_supported(int dtype, int kind, int mult, int64_t S, int nb, int64_t Ls, bool comp, int E, int minb) {
@@ -215,12 +215,19 @@ bool fused_supported(int dtype, int kind, int mult, int64_t S, int nb, int64_t L
     return conv1d_available(c, (int)staged_row(Ls));
 }
 
+bool cluster_supported(int dtype, int kind, int mult, int64_t S, int nb, int64_t Ls, int D, int E) {
+    if (kind == HD_HERMITIAN || D < 2 || !is_pow2(S) || S < 2 || S > max_fused_S(dtype)) return false;
+    Conv1dCfg c{dtype, kind, kernel_mult(mult), nb, (int)S, E, false, 1};
+    return conv1d_cluster_available(c, (int)staged_row(Ls), D);
+}
+
 bool mult_counts_ok(int mult, int A, int B) {
     return (mult == HD_MULT_PRODUCT && A == 2 && B == 1) || (mult == HD_MULT_SUM_PAIRS3 && A == 3 && B == 1) ||
-           (mult == HD_MULT_BASDEVANT2 && A == 2 && B == 2);
+           (mult == HD_MULT_BASDEVANT2 && A == 2 && B == 2) || (mult == HD_MULT_BASDEVANT3 && A == 3 && B == 5);
 }
 
 int kernel_mult(int mult) {
+    if (mult == HD_MULT_BASDEVANT3) return MULT_BASD3;
     return mult == HD_MULT_BASDEVANT2 ? MULT_BASD2 : (mult == HD_MULT_SUM_PAIRS3 ? MULT_PAIRS3 : MULT_PRODUCT);
 }
 
@@ -242,6 +249,16 @@ namespace hd {
 
 #define HD_SEL(fn, c, ...)                                                                   \
     do {                                                                                     \
+        if (c.mult == MULT_BASD3) {                                                          \
+            if (c.dtype == HD_F32) {                                                         \
+                if (c.kind == KIND_COMPLEX) return fn##_f32_complex_b5(__VA_ARGS__);         \
+                if (c.kind == KIND_CENTERED) return fn##_f32_centered_b5(__VA_ARGS__);       \
+                return fn##_f32_hermitian_b5(__VA_ARGS__);                                   \
+            }                                                                                \
+            if (c.kind == KIND_COMPLEX) return fn##_f64_complex_b5(__VA_ARGS__);             \
+            if (c.kind == KIND_CENTERED) return fn##_f64_centered_b5(__VA_ARGS__);           \
+            return fn##_f64_hermitian_b5(__VA_ARGS__);                                       \
+        }                                                                                    \
         if (c.mult == MULT_BASD2) {                                                          \
             if (c.dtype == HD_F32) {                                                         \
                 if (c.kind == KIND_COMPLEX) return fn##_f32_complex_b2(__VA_ARGS__);         \
@@ -270,6 +287,12 @@ int conv1d_variants(int dtype, int kind, Conv1dCfg* out, int cap) {
     HD_SEL(conv1d_variants, c, out, cap);
 }
 cudaError_t conv1d_launch(const Conv1dCfg& c, const ConvArgs& a, cudaStream_t st) { HD_SEL(conv1d_launch, c, c, a, st); }
+bool conv1d_cluster_available(const Conv1dCfg& c, int ls_pad, int D) {
+    HD_SEL(conv1d_cluster_available, c, c, ls_pad, D);
+}
+cudaError_t conv1d_cluster_launch(const Conv1dCfg& c, const ConvArgs& a, int D, cudaStream_t st) {
+    HD_SEL(conv1d_cluster_launch, c, c, a, D, st);
+}
 cudaError_t forward_residue_launch(const Conv1dCfg& c, const ConvArgs& a, int r, int m, void* out, cudaStream_t st) {
     HD_SEL(forward_residue_launch, c, c, a, r, m, out, st);
 }
@@ -285,12 +308,15 @@ hd_status hd_device_status(void) {
         cudaGetLastError();
         return HD_ERR_CUDA;
     }
-    const int e[12] = {conv1d_take_error_f32_complex(),     conv1d_take_error_f32_centered(),
+    const int e[18] = {conv1d_take_error_f32_complex(),     conv1d_take_error_f32_centered(),
                        conv1d_take_error_f32_hermitian(),   conv1d_take_error_f64_complex(),
                        conv1d_take_error_f64_centered(),    conv1d_take_error_f64_hermitian(),
                        conv1d_take_error_f32_complex_b2(),  conv1d_take_error_f32_centered_b2(),
                        conv1d_take_error_f32_hermitian_b2(), conv1d_take_error_f64_complex_b2(),
-                       conv1d_take_error_f64_centered_b2(), conv1d_take_error_f64_hermitian_b2()};
+                       conv1d_take_error_f64_centered_b2(), conv1d_take_error_f64_hermitian_b2(),
+                       conv1d_take_error_f32_complex_b5(),  conv1d_take_error_f32_centered_b5(),
+                       conv1d_take_error_f32_hermitian_b5(), conv1d_take_error_f64_complex_b5(),
+                       conv1d_take_error_f64_centered_b5(), conv1d_take_error_f64_hermitian_b5()};
     hd_status st = HD_OK;
     for (int v : e) {
         if (v < 0) return HD_ERR_CUDA;
@@ -341,7 +367,9 @@ hd_status hd_derive_params(int kind, int64_t L, int64_t M, int64_t m, int64_t* p
 
 int64_t hd_dealias_bound(int kind, int mult, int64_t L) {
     // every output of every mult is a (signed) sum of binary products
-    if (L <= 0 || (mult != HD_MULT_PRODUCT && mult != HD_MULT_SUM_PAIRS3 && mult != HD_MULT_BASDEVANT2)) return -1;
+    if (L <= 0 || (mult != HD_MULT_PRODUCT && mult != HD_MULT_SUM_PAIRS3 && mult != HD_MULT_BASDEVANT2 &&
+                   mult != HD_MULT_BASDEVANT3))
+        return -1;
     if (kind == HD_COMPLEX) return 2 * L - 1;
     if (kind == HD_CENTERED) return L + L / 2;
     if (kind == HD_HERMITIAN) {
@@ -365,7 +393,7 @@ hd_status hd_plan_create(hd_plan** out, int64_t L, int64_t M, int A, int B, int6
     d.B = B;
     d.kind = HD_COMPLEX;
     d.dtype = HD_F32;
-    d.mult = B == 2 ? HD_MULT_BASDEVANT2 : (A == 2 ? HD_MULT_PRODUCT : HD_MULT_SUM_PAIRS3);
+    d.mult = B == 5 ? HD_MULT_BASDEVANT3 : (B == 2 ? HD_MULT_BASDEVANT2 : (A == 2 ? HD_MULT_PRODUCT : HD_MULT_SUM_PAIRS3));
     d.m[0] = m;
     d.p[0] = p;
     d.q[0] = q;

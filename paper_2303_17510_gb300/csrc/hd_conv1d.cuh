@@ -37,26 +37,37 @@
 // (COMP), plain below; FP64 is plain.
 #pragma once
 
+#include <cooperative_groups.h>
+
 #include "hd_fft.cuh"
 
 namespace hd {
 
 enum { KIND_COMPLEX = 0, KIND_CENTERED = 1, KIND_HERMITIAN = 2 };
-enum { MULT_PRODUCT = 0, MULT_PAIRS3 = 1, MULT_BASD2 = 2 };
+enum { MULT_PRODUCT = 0, MULT_PAIRS3 = 1, MULT_BASD2 = 2, MULT_BASD3 = 3 };
 
-// Inputs A and outputs B of each mult; NX = max(A, B) exchange buffers.
+// Inputs A and outputs B of each mult; NX exchange buffers.
 //   MULT_PRODUCT  A = 2, B = 1:  F1 F2
 //   MULT_PAIRS3   A = 3, B = 1:  F1 F2 + F2 F3 + F3 F1
 //   MULT_BASD2    A = 2, B = 2:  (F1 F2, F1^2 - F2^2), the nonlinear terms of
 //                 2D incompressible Navier-Stokes in Basdevant's form
 //                 (velocity components in; Section 9 counts A = B = 2)
+//   MULT_BASD3    A = 3, B = 5:  (F1 F2, F2 F3, F3 F1, F1^2 - F3^2, F2^2 - F3^2),
+//                 the same for 3D (Section 9 counts A = 3, B = 5)
+// With B <= 2 the residue sums live in registers and the B inverse
+// transforms run together (NX = max(A, B) buffers).  With more outputs
+// (OUT_SMEM) the sums live in shared memory, ACC = B * 2 * S values per group
+// (each thread owns its own entries), and the inverse transforms run one
+// output at a time from the forward spectra kept in registers (NX = A).
 template <int MULT>
 struct MultShape {
-    static constexpr int A = MULT == MULT_PAIRS3 ? 3 : 2;
-    static constexpr int B = MULT == MULT_BASD2 ? 2 : 1;
-    static constexpr int NX = A > B ? A : B;
+    static constexpr int A = (MULT == MULT_PAIRS3 || MULT == MULT_BASD3) ? 3 : 2;
+    static constexpr int B = MULT == MULT_BASD2 ? 2 : (MULT == MULT_BASD3 ? 5 : 1);
+    static constexpr bool OUT_SMEM = B > 2;
+    static constexpr int NX = OUT_SMEM ? A : (A > B ? A : B);
+    __host__ __device__ static constexpr int acc(int S) { return OUT_SMEM ? B * 2 * S : 0; }
 };
-constexpr int kMaxOut = 2;
+constexpr int kMaxOut = 5;
 
 // arithmetic of mult on complex or real values
 __device__ __forceinline__ float xmul(float a, float b) { return a * b; }
@@ -80,9 +91,30 @@ __device__ __forceinline__ void mult_point(const X* x, X* y) {
         y[0] = xmul(x[0], x[XS]);
     } else if constexpr (MULT == MULT_PAIRS3) {   // F1F2 + F2F3 + F3F1 = F1 F2 + F3 (F1 + F2)
         y[0] = xadd(xmul(x[0], x[XS]), xmul(x[2 * XS], xadd(x[0], x[XS])));
-    } else {                                       // F1 F2, F1^2 - F2^2 = (F1 + F2)(F1 - F2)
+    } else if constexpr (MULT == MULT_BASD2) {     // F1 F2, F1^2 - F2^2 = (F1 + F2)(F1 - F2)
         y[0] = xmul(x[0], x[XS]);
         y[YS] = xmul(xadd(x[0], x[XS]), xsub(x[0], x[XS]));
+    } else {
+        static_assert(MULT == MULT_BASD3, "mult");
+        y[0] = xmul(x[0], x[XS]);
+        y[YS] = xmul(x[XS], x[2 * XS]);
+        y[2 * YS] = xmul(x[2 * XS], x[0]);
+        y[3 * YS] = xmul(xadd(x[0], x[2 * XS]), xsub(x[0], x[2 * XS]));
+        y[4 * YS] = xmul(xadd(x[XS], x[2 * XS]), xsub(x[XS], x[2 * XS]));
+    }
+}
+
+// output b of mult at one point (the OUT_SMEM path, one output at a time)
+template <int MULT, int XS, class X>
+__device__ __forceinline__ X mult_out(const X* x, int b) {
+    static_assert(MULT == MULT_BASD3, "outputs one at a time: the 3D Basdevant mult");
+    const X x0 = x[0], x1 = x[XS], x2 = x[2 * XS];
+    switch (b) {
+        case 0: return xmul(x0, x1);
+        case 1: return xmul(x1, x2);
+        case 2: return xmul(x2, x0);
+        case 3: return xmul(xadd(x0, x2), xsub(x0, x2));
+        default: return xmul(xadd(x1, x2), xsub(x1, x2));
     }
 }
 
@@ -184,8 +216,19 @@ __device__ __forceinline__ void conv1d_body(const ConvArgs& a, int64_t inst, boo
     constexpr int TT = Sh::T;
     constexpr int A = MultShape<MULT>::A;
     constexpr int B = MultShape<MULT>::B;
+    constexpr bool OSM = MultShape<MULT>::OUT_SMEM;
+    constexpr int BR = OSM ? 1 : B;   // outputs whose residue sums live in registers
     const T* twN = static_cast<const T*>(a.twN);
     const TwGlobal<T> twS{static_cast<const T*>(a.twS)};
+    // OUT_SMEM: residue sums of output b, block nb at acc[(b NB + nb) S + j], each
+    // entry read and written only by the thread that owns slot j
+    T* acc = sm + MultShape<MULT>::NX * Sh::SMEM;
+    if constexpr (OSM) {
+#pragma unroll 1
+        for (int b = 0; b < B * NB; ++b)
+#pragma unroll
+            for (int e = 0; e < E; ++e) acc[b * S + tau + TT * e] = czero<T>();
+    }
 
     if constexpr (STAGE) {
         // stage the A inputs of this convolution in shared memory (coalesced)
@@ -201,20 +244,20 @@ __device__ __forceinline__ void conv1d_body(const ConvArgs& a, int64_t inst, boo
     }
 
     // residue sums of output b at [b * 2E + 2e (+1)]
-    R s0[B * 2 * E], c0[COMP ? B * 2 * E : 1];
-    R s1[NB == 2 ? B * 2 * E : 1], c1[(NB == 2 && COMP) ? B * 2 * E : 1];
+    R s0[BR * 2 * E], c0[COMP ? BR * 2 * E : 1];
+    R s1[NB == 2 ? BR * 2 * E : 1], c1[(NB == 2 && COMP) ? BR * 2 * E : 1];
 #pragma unroll
-    for (int e = 0; e < B * 2 * E; ++e) s0[e] = R(0);
+    for (int e = 0; e < BR * 2 * E; ++e) s0[e] = R(0);
     if constexpr (COMP) {
 #pragma unroll
-        for (int e = 0; e < B * 2 * E; ++e) c0[e] = R(0);
+        for (int e = 0; e < BR * 2 * E; ++e) c0[e] = R(0);
     }
     if constexpr (NB == 2) {
 #pragma unroll
-        for (int e = 0; e < B * 2 * E; ++e) s1[e] = R(0);
+        for (int e = 0; e < BR * 2 * E; ++e) s1[e] = R(0);
         if constexpr (COMP) {
 #pragma unroll
-            for (int e = 0; e < B * 2 * E; ++e) c1[e] = R(0);
+            for (int e = 0; e < BR * 2 * E; ++e) c1[e] = R(0);
         }
     }
     R dummy = R(0);
@@ -247,6 +290,30 @@ __device__ __forceinline__ void conv1d_body(const ConvArgs& a, int64_t inst, boo
             }
             fft_forward<S, E, A>(v, sm, twS, tau);
             if (r == a.n - 1) consumed();
+            if constexpr (OSM) {
+                T twe[E];
+#pragma unroll
+                for (int e = 0; e < E; ++e) twe[e] = R0 ? mk<T>(1, 0) : ldtw(twr + tau + TT * e);
+#pragma unroll 1
+                for (int b = 0; b < B; ++b) {
+                    T p[E];
+#pragma unroll
+                    for (int e = 0; e < E; ++e) p[e] = mult_out<MULT, E>(v + e, b);
+                    fft_inverse<S, E, 1>(p, sm, twS, tau);
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        const int j = tau + TT * e;
+                        const T y = R0 ? p[e] : cmulc(p[e], twe[e]);      // zeta_N^{-r j} y_j
+                        T* q0 = acc + (b * NB) * S + j;
+                        *q0 = cadd(*q0, y);
+                        if constexpr (NB == 2) {
+                            T* q1 = acc + (b * NB + 1) * S + j;
+                            *q1 = cadd(*q1, R0 ? y : cmulc(y, cr));     // block 1: extra zeta_N^{-r S}
+                        }
+                    }
+                }
+                return;
+            }
             T p[B * E];
 #pragma unroll
             for (int e = 0; e < E; ++e) mult_point<MULT, E, E>(v + e, p + e);
@@ -298,6 +365,44 @@ __device__ __forceinline__ void conv1d_body(const ConvArgs& a, int64_t inst, boo
             }
             fft_forward<S, E, A>(v, sm, twS, tau);
             if (r1 + 2 >= a.n) consumed();
+            if constexpr (OSM) {
+#pragma unroll 1
+                for (int b = 0; b < B; ++b) {
+                    T p[E];
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        R xr[A], xi[A];
+#pragma unroll
+                        for (int aa = 0; aa < A; ++aa) {
+                            xr[aa] = v[aa * E + e].x;
+                            xi[aa] = v[aa * E + e].y;
+                        }
+                        p[e] = mk<T>(mult_out<MULT, 1>(xr, b), mult_out<MULT, 1>(xi, b));
+                    }
+                    fft_inverse<S, E, 1>(p, sm, twS, tau);
+#pragma unroll
+                    for (int e = 0; e < E; ++e) sm[padidx(tau + TT * e)] = p[e];
+                    __syncthreads();
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        const int j = tau + TT * e;
+                        const T t1 = R0 ? mk<T>(1, 0) : ldtw(twr1 + j);
+                        const T t2 = has2 ? ldtw(twr2 + j) : czero<T>();
+                        const T ym = sm[padidx((S - j) & (S - 1))];
+                        const T yj = p[e];
+                        const R hf = R(0.5);
+                        const T g1 = mk<T>((yj.x + ym.x) * hf, (yj.y - ym.y) * hf);
+                        const T d = mk<T>(yj.x - ym.x, yj.y + ym.y);
+                        const T g2 = mk<T>(d.y * hf, -d.x * hf);
+                        T y = R0 ? g1 : cmulc(g1, t1);
+                        if (has2) y = cadd(y, cmulc(g2, t2));
+                        T* q = acc + b * S + j;
+                        *q = cadd(*q, y);
+                    }
+                    __syncthreads();
+                }
+                return;
+            }
             // real parts carry residue r1, imaginary parts residue r2: mult on each
             T p[B * E];
 #pragma unroll
@@ -355,15 +460,20 @@ __device__ __forceinline__ void conv1d_body(const ConvArgs& a, int64_t inst, boo
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             const int j = tau + TT * e;
-            const int o = b * 2 * E + 2 * e;
-            const R x0 = COMP ? s0[o] + c0[o] : s0[o];
-            const R y0 = COMP ? s0[o + 1] + c0[o + 1] : s0[o + 1];
-            const T o0 = mk<T>(x0 * sc, y0 * sc);
-            T o1 = czero<T>();
-            if constexpr (NB == 2) {
-                const R x1 = COMP ? s1[o] + c1[o] : s1[o];
-                const R y1 = COMP ? s1[o + 1] + c1[o + 1] : s1[o + 1];
-                o1 = mk<T>(x1 * sc, y1 * sc);
+            T o0, o1 = czero<T>();
+            if constexpr (OSM) {
+                o0 = cscale(acc[(b * NB) * S + j], sc);
+                if constexpr (NB == 2) o1 = cscale(acc[(b * NB + 1) * S + j], sc);
+            } else {
+                const int o = b * 2 * E + 2 * e;
+                const R x0 = COMP ? s0[o] + c0[o] : s0[o];
+                const R y0 = COMP ? s0[o + 1] + c0[o + 1] : s0[o + 1];
+                o0 = mk<T>(x0 * sc, y0 * sc);
+                if constexpr (NB == 2) {
+                    const R x1 = COMP ? s1[o] + c1[o] : s1[o];
+                    const R y1 = COMP ? s1[o + 1] + c1[o + 1] : s1[o + 1];
+                    o1 = mk<T>(x1 * sc, y1 * sc);
+                }
             }
             if constexpr (KIND == KIND_COMPLEX) {
                 if (j < a.L) __stcs(hout + j, o0);
@@ -397,7 +507,7 @@ __global__ void __launch_bounds__(ConvLaunch<S, E>::MAXT, MINB) conv1d_kernel(co
     const int G = blockDim.x / TT;
     const int g = threadIdx.x / TT;
     const int tau = threadIdx.x - g * TT;
-    T* st = reinterpret_cast<T*>(smem_raw) + (size_t)g * (A * a.ls_pad + NX * Sh::SMEM);
+    T* st = reinterpret_cast<T*>(smem_raw) + (size_t)g * (A * a.ls_pad + NX * Sh::SMEM + MultShape<MULT>::acc(S));
     T* sm = st + A * a.ls_pad;
     const int64_t inst = (int64_t)blockIdx.x * G + g;
     conv1d_body<R, S, E, KIND, MULT, NB, COMP>(a, inst, inst < a.count, tau, st, sm);
@@ -480,7 +590,7 @@ __global__ void __launch_bounds__(ConvLaunch<S, E>::MAXT, MINB) conv1d_kernel_pi
     const int tau = threadIdx.x - g * TT;
     const size_t stage_elems = (size_t)G * A * a.ls_pad;          // one staging buffer (all groups)
     T* stage0 = reinterpret_cast<T*>(smem_raw);
-    T* sm = stage0 + NBUF * stage_elems + (size_t)g * NX * Sh::SMEM;
+    T* sm = stage0 + NBUF * stage_elems + (size_t)g * (NX * Sh::SMEM + MultShape<MULT>::acc(S));
     const int64_t nsteps = (a.count + G - 1) / G;                    // CTA steps over the batch
     const uint32_t row_bytes = (uint32_t)(a.Ls * sizeof(T));
 
@@ -537,6 +647,155 @@ __global__ void __launch_bounds__(ConvLaunch<S, E>::MAXT, MINB) conv1d_kernel_pi
         }
         __syncthreads();
     }
+}
+
+// ---------------------------------------------------------------------------
+// Cluster variant for few convolutions (D > 1 residues per pass, Section 6.5).
+//
+// A convolution that runs alone on one CTA is bound by that SM's arithmetic
+// (most of all in FP64).  Residue contributions are independent and add up
+// (Section 2.2), so here one convolution runs on a thread-block cluster of
+// D * A CTAs: CTA c takes residue group g = c / A (residues r = g, g + D, ...)
+// and input ai = c % A.  Per residue, every CTA folds, twists and transforms
+// its own input; the CTAs with ai > 0 publish their spectra in shared memory
+// (two buffers, alternating between residues); after a cluster barrier the
+// group's CTA ai = 0 reads them through distributed shared memory, applies
+// mult, runs the inverse transform and accumulates.  At the end each group's
+// scaled partial sums are written to shared memory, and every CTA of the
+// cluster sums a slice of the outputs over the D groups in a fixed order
+// (deterministic) and stores it.  Complex and centered kinds, one output.
+// Residue sums are plain.  A lone convolution is latency-bound, so each CTA
+// copies its FFT twiddles into shared memory once, together with the input
+// row, and each residue's twist row before its fold.
+template <class R, int S, int E, int KIND, int MULT, int NB>
+__global__ void __launch_bounds__(S / E) conv1d_cluster_kernel(const __grid_constant__ ConvArgs a, int D) {
+    using T = cplx<R>;
+    using Sh = FftShape<S, E>;
+    constexpr int TT = Sh::T;
+    constexpr int A = MultShape<MULT>::A;
+    static_assert(MultShape<MULT>::B == 1 && KIND != KIND_HERMITIAN, "cluster variant: one output, not Hermitian");
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const int CL = D * A;
+    const int c = (int)cl.block_rank();
+    const int g = c / A, ai = c - g * A;
+    const int64_t inst = blockIdx.x / CL;
+    const int tau = threadIdx.x;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* st = reinterpret_cast<T*>(smem_raw);   // staged input ai (ls_pad values); the partial sums at the end
+    T* sm = st + a.ls_pad;                      // FFT exchange buffer
+    T* spec = sm + Sh::SMEM;                    // published spectra: two buffers of S values
+    T* tws = spec + 2 * S;                      // FFT pass twiddles (TW_TOTAL values)
+    T* twr = tws + (Sh::TW_TOTAL > 0 ? Sh::TW_TOTAL : 1);   // twists of the current residue (S values)
+    const T* twN = static_cast<const T*>(a.twN);
+    const T* twg = static_cast<const T*>(a.twS);
+    const TwShared<T> twS{tws};
+    const T* src = static_cast<const T*>(a.f[ai]) + inst * a.stride;
+    for (int i = tau; i < a.Ls; i += TT) st[i] = src[i];
+    for (int i = tau; i < Sh::TW_TOTAL; i += TT) tws[i] = __ldg(twg + i);
+    __syncthreads();
+
+    R s0[2 * E], s1[NB == 2 ? 2 * E : 1];
+#pragma unroll
+    for (int e = 0; e < 2 * E; ++e) {
+        s0[e] = R(0);
+        if constexpr (NB == 2) s1[e] = R(0);
+    }
+    R dummy = R(0);
+    const int nsteps = (a.n + D - 1) / D;
+    for (int k = 0; k < nsteps; ++k) {
+        const int r = g + k * D;
+        const bool act = r < a.n;             // uniform over the CTA
+        T* spk = spec + (k & 1) * S;
+        T cr = ldtw(twN + (int64_t)a.n * S + (act ? r : 0));   // zeta_N^{r S}
+        if constexpr (KIND == KIND_CENTERED) cr = cconj(cr);
+        T v[E];
+        if (act) {
+            // this residue's twists zeta_N^{r j}, once every thread has finished
+            // the previous residue's accumulation (which reads the old row)
+            __syncthreads();
+            const T* row = twN + (int64_t)r * S;
+            for (int i = tau; i < S; i += TT) twr[i] = __ldg(row + i);
+            __syncthreads();
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int j = tau + TT * e;
+                const T tw = twr[j];
+                if constexpr (KIND == KIND_COMPLEX && NB == 1) {
+                    const T x = j < a.L ? st[j] : czero<T>();
+                    v[e] = cmul(x, tw);
+                } else {
+                    T b0, b1;
+                    load_fold<KIND>(st, j, S, a, true, b0, b1);
+                    v[e] = cmul(cadd(b0, cmul(cr, b1)), tw);
+                }
+            }
+            fft_forward<S, E, 1>(v, sm, twS, tau);
+            if (ai != 0) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) spk[e * TT + tau] = v[e];
+            }
+        }
+        cl.sync();                             // spectra of residue r published
+        if (act && ai == 0) {
+            T x[A * E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) x[e] = v[e];
+#pragma unroll
+            for (int aa = 1; aa < A; ++aa) {
+                const T* rem = cl.map_shared_rank(spk, (unsigned)(g * A + aa));
+#pragma unroll
+                for (int e = 0; e < E; ++e) x[aa * E + e] = rem[e * TT + tau];
+            }
+            T p[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) mult_point<MULT, E, E>(x + e, p + e);
+            fft_inverse<S, E, 1>(p, sm, twS, tau);
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int j = tau + TT * e;
+                const T y = cmulc(p[e], twr[j]);          // zeta_N^{-r j} y_j
+                acc_add<R, false>(s0[2 * e], dummy, y.x);
+                acc_add<R, false>(s0[2 * e + 1], dummy, y.y);
+                if constexpr (NB == 2) {
+                    const T y1 = cmulc(y, cr);            // block 1: extra zeta_N^{-r S}
+                    acc_add<R, false>(s1[2 * e], dummy, y1.x);
+                    acc_add<R, false>(s1[2 * e + 1], dummy, y1.y);
+                }
+            }
+        }
+        // the next residue publishes into the other buffer; the one after that
+        // reuses this one only after the next cluster barrier, which every
+        // reader of this buffer reaches after its reads
+    }
+    __syncthreads();                           // st is no longer read: it takes the partial sums
+    if (ai == 0) {
+        const R sc = R(a.invN);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int j = tau + TT * e;
+            const T o0 = mk<T>(s0[2 * e] * sc, s0[2 * e + 1] * sc);
+            if constexpr (KIND == KIND_COMPLEX) {
+                if (j < a.L) st[j] = o0;
+                if constexpr (NB == 2) {
+                    if (j + S < a.L) st[j + S] = mk<T>(s1[2 * e] * sc, s1[2 * e + 1] * sc);
+                }
+            } else {
+                if (j < a.L - a.H) st[j + a.H] = o0;
+                if (j >= S - a.H) st[j - S + a.H] = mk<T>(s1[2 * e] * sc, s1[2 * e + 1] * sc);
+            }
+        }
+    }
+    cl.sync();                                 // partial sums of every group written
+    const int chunk = (a.Ls + CL - 1) / CL;
+    const int i1 = (c + 1) * chunk < a.Ls ? (c + 1) * chunk : a.Ls;
+    T* hout = static_cast<T*>(a.h[0]) + inst * a.stride;
+    for (int i = c * chunk + tau; i < i1; i += TT) {
+        T sum = czero<T>();
+        for (int gg = 0; gg < D; ++gg) sum = cadd(sum, cl.map_shared_rank(st, (unsigned)(gg * A))[i]);
+        hout[i] = sum;
+    }
+    cl.sync();                                 // no CTA leaves while others read its shared memory
 }
 
 // Forward transform of one residue of one input, written in the paper's

@@ -4,6 +4,7 @@
 #define HD_DT f32
 #define HD_KN hermitian
 #define HD_VARIANTS HD_VARIANTS_F32
+#define HD_CLUSTER_VARIANTS HD_CLUSTER_VARIANTS_F32
 #define HD_UNIT_MULTS(Y, ...) Y(MULT_PRODUCT, __VA_ARGS__) Y(MULT_PAIRS3, __VA_ARGS__)
 #include "hd_conv1d_variants.h"
 #include "hd_conv1d_tu.cuh"

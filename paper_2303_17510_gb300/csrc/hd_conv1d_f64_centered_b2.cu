@@ -4,6 +4,7 @@
 #define HD_DT f64
 #define HD_KN centered_b2
 #define HD_VARIANTS HD_VARIANTS_F64
+#define HD_CLUSTER_VARIANTS HD_CLUSTER_VARIANTS_F64
 #define HD_UNIT_MULTS(Y, ...) Y(MULT_BASD2, __VA_ARGS__)
 #include "hd_conv1d_variants.h"
 #include "hd_conv1d_tu.cuh"

@@ -15,7 +15,8 @@ namespace {
 template <class R, int S, int E, int MULT>
 size_t group_smem(int ls_pad) {
     using MS = MultShape<MULT>;
-    return (size_t(MS::A) * size_t(ls_pad) + size_t(MS::NX) * FftShape<S, E>::SMEM) * sizeof(cplx<R>);
+    return (size_t(MS::A) * size_t(ls_pad) + size_t(MS::NX) * FftShape<S, E>::SMEM + size_t(MS::acc(S))) *
+           sizeof(cplx<R>);
 }
 
 template <class R, int S, int E, int MULT>
@@ -69,7 +70,7 @@ cudaError_t launch_pipe(const ConvArgs& a0, cudaStream_t st, bool* used) {
     if ((a0.stride * esz) % 16 != 0 || (a0.Ls * esz) % 16 != 0 || (a0.ls_pad * esz) % 16 != 0) return cudaSuccess;
     int G = 256 / T;
     if (G < 1) G = 1;
-    const size_t fft = size_t(NX) * FftShape<S, E>::SMEM * esz;
+    const size_t fft = (size_t(NX) * FftShape<S, E>::SMEM + size_t(MultShape<MULT>::acc(S))) * esz;
     const size_t stg = size_t(A) * a0.ls_pad * esz;
     while (G > 1 && G * (NBUF * stg + fft) > kMaxSmemPerBlock - 64) --G;
     const size_t smem = size_t(G) * (NBUF * stg + fft);
@@ -137,6 +138,60 @@ cudaError_t launch_fwd(const ConvArgs& a, int r, int m, void* out, cudaStream_t 
     return cudaGetLastError();
 }
 
+// Cluster variant: D residue groups x A inputs CTAs per convolution (complex
+// and centered kinds, one output).  Shared memory: the staged row, one
+// exchange buffer, two published spectra, the FFT twiddles and one twist row.
+template <class R, int S, int E>
+size_t cluster_smem(int ls_pad) {
+    using Sh = FftShape<S, E>;
+    return (size_t(ls_pad) + Sh::SMEM + 3 * size_t(S) + (Sh::TW_TOTAL > 0 ? Sh::TW_TOTAL : 1)) * sizeof(cplx<R>);
+}
+
+template <int MULT>
+constexpr bool cluster_ok() {
+    return HD_KIND != KIND_HERMITIAN && MultShape<MULT>::B == 1;
+}
+
+template <int S, int E, int MULT, int NB>
+bool cluster_fits(int ls_pad, int D) {
+    if constexpr (!cluster_ok<MULT>() || (HD_KIND == KIND_CENTERED && NB != 2)) {
+        return false;
+    } else {
+        const int CL = D * MultShape<MULT>::A;
+        return D >= 2 && CL <= 8 && cluster_smem<HD_REAL, S, E>(ls_pad) <= kMaxSmemPerBlock;
+    }
+}
+
+template <int S, int E, int MULT, int NB>
+cudaError_t launch_cluster(const ConvArgs& a, int D, cudaStream_t st) {
+    if constexpr (!cluster_ok<MULT>() || (HD_KIND == KIND_CENTERED && NB != 2)) {
+        return cudaErrorInvalidValue;
+    } else {
+        if (!cluster_fits<S, E, MULT, NB>(a.ls_pad, D)) return cudaErrorInvalidValue;
+        if (a.count <= 0) return cudaSuccess;
+        const int CL = D * MultShape<MULT>::A;
+        const size_t smem = cluster_smem<HD_REAL, S, E>(a.ls_pad);
+        auto k = conv1d_cluster_kernel<HD_REAL, S, E, HD_KIND, MULT, NB>;
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(a.count * CL));
+        cfg.blockDim = dim3(S / E);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)CL;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, k, a, D);
+    }
+}
+
 // Hermitian data folds into one output block, centered data into two;
 // compensated accumulation is an FP32 option.
 template <int MULT, int NB, bool COMP>
@@ -195,6 +250,25 @@ cudaError_t HD_FN(conv1d_launch_, HD_DT, HD_KN)(const Conv1dCfg& c, const ConvAr
 cudaError_t HD_FN(forward_residue_launch_, HD_DT, HD_KN)(const Conv1dCfg& c, const ConvArgs& a, int r, int m,
                                                          void* out, cudaStream_t st) {
     HD_VARIANTS(HD_FWD_CASE)
+    return cudaErrorInvalidValue;
+}
+
+#define HD_CLUSTER_MULT(MU, SS, EE, FN, ...)                                                          \
+    if (c.mult == MU && c.nb == 1) return FN<SS, EE, MU, 1>(__VA_ARGS__);                              \
+    if (c.mult == MU && c.nb == 2) return FN<SS, EE, MU, 2>(__VA_ARGS__);
+#define HD_CLUSTER_FITS_CASE(SS, EE) \
+    if (c.S == SS && c.E == EE) { HD_UNIT_MULTS(HD_CLUSTER_MULT, SS, EE, cluster_fits, ls_pad, D) }
+#define HD_CLUSTER_LAUNCH_CASE(SS, EE) \
+    if (c.S == SS && c.E == EE) { HD_UNIT_MULTS(HD_CLUSTER_MULT, SS, EE, launch_cluster, a, D, st) }
+
+bool HD_FN(conv1d_cluster_available_, HD_DT, HD_KN)(const Conv1dCfg& c, int ls_pad, int D) {
+    HD_CLUSTER_VARIANTS(HD_CLUSTER_FITS_CASE)
+    return false;
+}
+
+cudaError_t HD_FN(conv1d_cluster_launch_, HD_DT, HD_KN)(const Conv1dCfg& c, const ConvArgs& a, int D,
+                                                        cudaStream_t st) {
+    HD_CLUSTER_VARIANTS(HD_CLUSTER_LAUNCH_CASE)
     return cudaErrorInvalidValue;
 }
 

@@ -26,6 +26,10 @@ constexpr size_t kMaxSmemPerBlock = 227 * 1024;
 bool conv1d_available(const Conv1dCfg& c, int ls_pad);
 // launch `count` convolutions (a.count) of cfg on stream
 cudaError_t conv1d_launch(const Conv1dCfg& c, const ConvArgs& a, cudaStream_t st);
+// cluster variant (D residue groups per convolution, D > 1): available for
+// cfg (S, E, kind, mult, nb) with rows of ls_pad values, and its launch
+bool conv1d_cluster_available(const Conv1dCfg& c, int ls_pad, int D);
+cudaError_t conv1d_cluster_launch(const Conv1dCfg& c, const ConvArgs& a, int D, cudaStream_t st);
 // compiled (S, E, minb) variants for cfg's dtype and kind; returns the count
 int conv1d_variants(int dtype, int kind, Conv1dCfg* out, int cap);
 // forward transform of residue r of one input (debug path)
@@ -45,13 +49,16 @@ int col_E_of_f32(int S);
 int col_E_of_f64(int S);
 
 // per translation unit entry points (dtype x kind x mult set: the
-// single-output mults, and the two-output one in the _b2 units)
+// single-output mults, the two-output one in the _b2 units, the five-output
+// one in the _b5 units)
 #define HD_DECL_TU(DT, KN)                                                                                   \
     bool conv1d_available_##DT##_##KN(const Conv1dCfg& c, int ls_pad);                                                    \
     cudaError_t conv1d_launch_##DT##_##KN(const Conv1dCfg& c, const ConvArgs& a, cudaStream_t st);            \
     cudaError_t forward_residue_launch_##DT##_##KN(const Conv1dCfg& c, const ConvArgs& a, int r, int m,       \
                                                     void* out, cudaStream_t st);                              \
     int conv1d_variants_##DT##_##KN(Conv1dCfg* out, int cap);                                                \
+    bool conv1d_cluster_available_##DT##_##KN(const Conv1dCfg& c, int ls_pad, int D);                          \
+    cudaError_t conv1d_cluster_launch_##DT##_##KN(const Conv1dCfg& c, const ConvArgs& a, int D, cudaStream_t st); \
     int conv1d_take_error_##DT##_##KN();
 HD_DECL_TU(f32, complex)
 HD_DECL_TU(f32, centered)
@@ -65,6 +72,12 @@ HD_DECL_TU(f32, hermitian_b2)
 HD_DECL_TU(f64, complex_b2)
 HD_DECL_TU(f64, centered_b2)
 HD_DECL_TU(f64, hermitian_b2)
+HD_DECL_TU(f32, complex_b5)
+HD_DECL_TU(f32, centered_b5)
+HD_DECL_TU(f32, hermitian_b5)
+HD_DECL_TU(f64, complex_b5)
+HD_DECL_TU(f64, centered_b5)
+HD_DECL_TU(f64, hermitian_b5)
 #undef HD_DECL_TU
 
 }  // namespace hd

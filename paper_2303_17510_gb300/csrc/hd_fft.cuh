@@ -255,6 +255,13 @@ struct TwGlobal {
     __device__ __forceinline__ T operator()(int idx) const { return __ldg(p + idx); }
 };
 
+// Twiddle source for the FFT passes: the same table copied into shared memory.
+template <class T>
+struct TwShared {
+    const T* p;
+    __device__ __forceinline__ T operator()(int idx) const { return p[idx]; }
+};
+
 // Pass k on NA independent arrays held back to back in v (array a in
 // v[a*E .. a*E+E)): radix-R DFT, then the twiddle zeta_{N_k}^{c k1} (forward);
 // the inverse applies the conjugate twiddle first, then the inverse DFT.  The

@@ -228,10 +228,14 @@ hd_status plan_create_nd(hd_plan** out, const hd_desc* d) {
         pl->scratch_bytes += (size_t)elems * esz;
         inst *= nr * ax.S;
     }
+    // the sub-convolutions write their outputs over their inputs, which residue
+    // blocks of the split path would read again after the first block
+    if (st == HD_OK && pl->ax[nd - 1].path == PATH_SPLIT && split_block(pl->ax[nd - 1]) < pl->ax[nd - 1].n)
+        st = HD_ERR_UNSUPPORTED;
     // the innermost rows of the split path use the plan's chunked work buffer
     if (st == HD_OK && pl->ax[nd - 1].path == PATH_SPLIT) {
         AxisPlan& ax = pl->ax[nd - 1];
-        const size_t per = (size_t)d->A * (size_t)ax.n * (size_t)ax.S * esz;
+        const size_t per = (size_t)d->A * (size_t)split_block(ax) * (size_t)ax.S * esz;
         int64_t ch = (int64_t)((64u << 20) / per);   // as 1D plans: at most 64 MiB, L2-resident
         ax.chunk = ch < 1 ? 1 : (ch > 2048 ? 2048 : ch);
         if (cudaMalloc(&pl->scratch, per * (size_t)ax.chunk) != cudaSuccess) {

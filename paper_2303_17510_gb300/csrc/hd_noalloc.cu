@@ -49,7 +49,7 @@ extern "C" hd_status hd_convolve_batched_noalloc(const hd_plan* plan, int64_t co
         if (!h[b]) return HD_ERR_INVALID;
     if (count > 1 && batch_stride < plan->instance_elems) return HD_ERR_INVALID;
     const size_t esz = plan->dtype == HD_F64 ? 16 : 8;
-    const size_t per = (size_t)plan->A * (size_t)ax.n * (size_t)ax.S * esz;
+    const size_t per = (size_t)plan->A * (size_t)hd::split_block(ax) * (size_t)ax.S * esz;
     if (per > HD_NOALLOC_SCRATCH_BYTES) return HD_ERR_SCRATCH_LIMIT;
     if (count == 0) return HD_OK;
     hd::DeviceGuard guard(plan->device);   // the plan's device, as hd_convolve_batched does
@@ -64,6 +64,6 @@ extern "C" hd_status hd_convolve_batched_noalloc(const hd_plan* plan, int64_t co
     if (st != HD_OK) return st;
     const int64_t chunk = (int64_t)(HD_NOALLOC_SCRATCH_BYTES / per);
     st = hd::split_execute(*plan, ax, count, f, h, batch_stride, work, chunk, (cudaStream_t)stream);
-    if (st != HD_OK) const_cast<hd_plan*>(plan)->sticky = st;
+    if (st == HD_ERR_CUDA) const_cast<hd_plan*>(plan)->sticky = st;
     return st;
 }

@@ -178,7 +178,7 @@ hd_status plan_finish(const hd_desc* d, const AxisPlan& ax, hd_plan** out) {
             // instances at a time, at most 64 MiB so that the round trips
             // between the three phases stay in L2
             const size_t esz = d->dtype == HD_F64 ? 16 : 8;
-            const size_t per = (size_t)d->A * (size_t)a0.n * (size_t)a0.S * esz;
+            const size_t per = (size_t)d->A * (size_t)split_block(a0) * (size_t)a0.S * esz;
             int64_t ch = (int64_t)((64u << 20) / per);
             if (ch > 2048) ch = 2048;
             if (ch < 1) ch = 1;
@@ -208,6 +208,14 @@ hd_status axis_from_candidate(const hd_desc* d, const hd_candidate* c, AxisPlan*
     if (st != HD_OK && st != HD_ERR_UNSUPPORTED) return st;
     if (ax->S != c->S || ax->n != c->n) return HD_ERR_INVALID;
     ax->comp = c->comp != 0 && d->dtype == HD_F32;
+    if (ax->path == PATH_FUSED && c->D > 1 && d->kind != HD_HERMITIAN) {   // residue groups on a cluster
+        if (!cluster_supported(d->dtype, d->kind, d->mult, ax->S, ax->nb, ax->Ls, c->D, c->E) || c->D > ax->n)
+            return HD_ERR_UNSUPPORTED;
+        ax->E = c->E;
+        ax->minb = 1;
+        ax->comp = false;
+        return HD_OK;
+    }
     if (ax->path == PATH_FUSED) {
         ax->E = c->E;
         ax->minb = c->minb;
@@ -224,8 +232,10 @@ hd_status auto_axis(const hd_desc* d, AxisPlan* ax) {
     hd_candidate c;
     if (cache_lookup(d, &c) && axis_from_candidate(d, &c, ax) == HD_OK) return HD_OK;
     if (selector_installed() && d->B == 1) {   // trained on single-output mults
-        std::vector<hd_candidate> cands;
-        enumerate_candidates(d, &cands);
+        std::vector<hd_candidate> all, cands;
+        enumerate_candidates(d, &all);
+        for (auto& x : all)
+            if (single_group(d->kind, x)) cands.push_back(x);
         std::vector<int> pick, conf;
         if (!cands.empty() && selector_choose_batch({d}, {cands}, &pick, &conf) == HD_OK) {
             c = cands[pick[0]];
@@ -254,6 +264,14 @@ hd_status plan_create(hd_plan** out, const hd_desc* d) {
     else st = fill_axis(d->dtype, d->kind, d->mult, d->L[0], d->M[0], d->m[0], d->p[0], d->q[0], d->D[0], &ax);
     if (st != HD_OK) return st;
     if (d->D[0] > 0) ax.D = d->D[0];
+    if (ax.D > 1 && d->kind != HD_HERMITIAN && ax.path == PATH_FUSED) {   // D residue groups at once: the cluster variant
+        const int ce = cluster_default_E(d->dtype, ax.S);
+        if (ax.D > ax.n || !cluster_supported(d->dtype, d->kind, d->mult, ax.S, ax.nb, ax.Ls, ax.D, ce))
+            return HD_ERR_UNSUPPORTED;
+        ax.E = ce;
+        ax.minb = 1;
+        ax.comp = false;
+    }
     return plan_finish(d, ax, out);
 }
 
@@ -312,18 +330,32 @@ SplitArgs make_split_args(const hd_plan& pl, const AxisPlan& ax, int64_t first, 
     a.twS2 = ax.twS2;
     a.work = work;
     a.invN = 1.0 / (double)(ax.n * ax.S);
+    a.r0 = 0;
+    a.nr = (int)ax.n;
+    a.accumulate = 0;
     return a;
 }
 
 hd_status split_execute(const hd_plan& pl, const AxisPlan& ax, int64_t count, const void* const* f, void* const* h,
                         int64_t stride, void* work, int64_t chunk, cudaStream_t st) {
     const int mult = kernel_mult(pl.mult);
+    const int64_t blk = split_block(ax);
+    // residue blocks re-read the inputs after the first block has written the
+    // output, so blocked plans cannot write over their inputs
+    if (blk < ax.n)
+        for (int a = 0; a < pl.A; ++a)
+            if (f[a] == h[0]) return HD_ERR_INVALID;
     for (int64_t first = 0; first < count; first += chunk) {
         const int64_t cnt = count - first < chunk ? count - first : chunk;
         SplitArgs a = make_split_args(pl, ax, first, cnt, f, h, stride, work);
-        cudaError_t e = pl.dtype == HD_F64 ? split_launch_f64(a, ax.kind, mult, ax.comp, st)
-                                           : split_launch_f32(a, ax.kind, mult, ax.comp, st);
-        if (e != cudaSuccess) return HD_ERR_CUDA;
+        for (int64_t r0 = 0; r0 < ax.n; r0 += blk) {
+            a.r0 = (int)r0;
+            a.nr = (int)(ax.n - r0 < blk ? ax.n - r0 : blk);
+            a.accumulate = r0 > 0;
+            cudaError_t e = pl.dtype == HD_F64 ? split_launch_f64(a, ax.kind, mult, ax.comp, st)
+                                               : split_launch_f32(a, ax.kind, mult, ax.comp, st);
+            if (e != cudaSuccess) return HD_ERR_CUDA;
+        }
     }
     return HD_OK;
 }
@@ -347,11 +379,13 @@ hd_status plan_execute(hd_plan* pl, int64_t count, const void* const* f, void* c
     if (ax.path == PATH_SPLIT) {
         if (!pl->scratch) return HD_ERR_UNSUPPORTED;   // created without a work buffer
         hd_status s2 = split_execute(*pl, ax, count, f, h, stride, pl->scratch, ax.chunk, st);
-        if (s2 != HD_OK) pl->sticky = s2;
+        if (s2 == HD_ERR_CUDA) pl->sticky = s2;
         return s2;
     }
     ConvArgs a = make_conv_args(*pl, ax, count, f, h, stride);
-    cudaError_t e = conv1d_launch(fused_cfg(*pl, ax), a, st);
+    const bool cluster = ax.D > 1 && ax.kind != HD_HERMITIAN;
+    cudaError_t e = cluster ? conv1d_cluster_launch(fused_cfg(*pl, ax), a, ax.D, st)
+                            : conv1d_launch(fused_cfg(*pl, ax), a, st);
     if (e != cudaSuccess) {
         pl->sticky = HD_ERR_CUDA;
         return HD_ERR_CUDA;

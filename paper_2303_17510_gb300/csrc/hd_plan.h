@@ -55,6 +55,10 @@ struct AxisPlan {
     int64_t chunk;     // SPLIT: instances per scratch chunk
 };
 
+// Residues per block of the split path: D when 1 < D < n (blocks accumulate
+// into the output), else all n residues in one block.
+inline int64_t split_block(const AxisPlan& ax) { return (ax.D > 1 && ax.D < ax.n) ? ax.D : ax.n; }
+
 int64_t ceil_div(int64_t a, int64_t b);
 int64_t next_pow2_t(int64_t x);   // smallest power of two >= x
 bool is_pow2(int64_t x);
@@ -67,6 +71,15 @@ void axis_geometry(int kind, int64_t L, int64_t m, int64_t p, int64_t q, int64_t
 hd_status validate_axis(int kind, int mult, int64_t L, int64_t M, int64_t m, int64_t p, int64_t q, int64_t* S,
                         int64_t* n, int* nb);
 bool fused_supported(int dtype, int kind, int mult, int64_t S, int nb, int64_t Ls, bool comp, int E, int minb);
+// D > 1 residue groups of one convolution on a thread-block cluster (complex and
+// centered kinds, one output): true when the cluster kernel runs the fused axis
+bool cluster_supported(int dtype, int kind, int mult, int64_t S, int nb, int64_t Ls, int D, int E);
+// default values per thread of the cluster variant: 4 for FP64 (see
+// hd_conv1d_variants.h), 8 for FP32
+inline int cluster_default_E(int dtype, int64_t S) { return dtype == HD_F64 && S <= 1024 ? 4 : 8; }
+// candidates the learned selector and the ragged kernel consider: not the
+// cluster variants (their features are those of the D = 1 candidate)
+inline bool single_group(int kind, const hd_candidate& c) { return kind == HD_HERMITIAN || c.D <= 1; }
 int default_minb(int dtype, int64_t S, int mult);
 // split path (transforms larger than one CTA): S = S1 * S2, S2 the fused limit, S1 <= 16
 bool split_supported(int dtype, int kind, int mult, int64_t S, int nb);

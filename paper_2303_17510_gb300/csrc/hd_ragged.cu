@@ -212,6 +212,7 @@ size_t group_bytes() {
 // ragged feasibility of a candidate for one instance
 bool ragged_ok(const hd_desc* d, const hd_candidate& c) {
     const int64_t Ls = d->L[0];
+    if (!single_group(d->kind, c)) return false;   // the ragged kernel runs one residue at a time
     if (c.S <= 4096) {
         if (c.S < 8 || !is_pow2(c.S)) return false;
         return fused_tile_smem(c.S, d->A, (int)staged_row(Ls)) <= kSmemMax;

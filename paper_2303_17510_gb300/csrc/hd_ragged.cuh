@@ -128,6 +128,9 @@ __device__ __forceinline__ SplitArgs split_args_of(const RInst& r) {
     a.twS2 = r.twS2;
     a.work = r.work;
     a.invN = r.invN;
+    a.r0 = 0;
+    a.nr = r.n;
+    a.accumulate = 0;
     return a;
 }
 
@@ -137,7 +140,7 @@ __device__ __forceinline__ ConvArgs conv_args_of(const RInst& r) {
     a.f[1] = r.f[1];
     a.f[2] = r.f[2];
     a.h[0] = r.h;   // one output (B = 1)
-    a.h[1] = nullptr;
+    for (int b = 1; b < kMaxOut; ++b) a.h[b] = nullptr;
     a.stride = 0;
     a.count = 1;
     a.L = r.L;

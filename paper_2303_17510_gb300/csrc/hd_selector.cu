@@ -162,8 +162,10 @@ hd_status hd_selector_clear(void) {
 
 hd_status hd_selector_choose(const hd_desc* d, hd_candidate* out, int* confident) {
     if (!d || !out || d->ndim != 1) return HD_ERR_INVALID;
-    std::vector<hd_candidate> c;
-    enumerate_candidates(d, &c);
+    std::vector<hd_candidate> all, c;
+    enumerate_candidates(d, &all);
+    for (auto& x : all)
+        if (single_group(d->kind, x)) c.push_back(x);
     if (c.empty()) return HD_ERR_UNSUPPORTED;
     std::vector<int> pick, conf;
     hd_status st = selector_choose_batch({d}, {c}, &pick, &conf);

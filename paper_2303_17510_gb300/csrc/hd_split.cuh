@@ -18,6 +18,10 @@
 //                  twiddle and inverse DFT over k1, then the residue contribution
 //                  zeta_N^{-r i} y_{i mod S} accumulated into the output (all
 //                  residues in registers, one store).
+// Residues may run in blocks r0 .. r0 + nr - 1 (D residues per pass, Section
+// 6.5): the work buffer then holds A nr S values per instance, and the blocks
+// after the first add their contributions to the output (the output is the
+// accumulation buffer, so none is needed besides it).
 // Hermitian residues are not paired here: the residue's spectrum is real and
 // the inverse of a real spectrum is Hermitian, so y is used directly.
 #pragma once
@@ -38,8 +42,10 @@ struct SplitArgs {
     const void* twS;    // zeta_S^{j2 k1} at k1 S2 + j2 (k1 < S1, j2 < S2)
     const void* twR;    // residue twists (ConvArgs::twN layout)
     const void* twS2;   // FFT pass twiddles of the size-S2 row FFT
-    void* work;         // scratch: [instance][a][r][k1][j2]
+    void* work;         // scratch: [instance][a][r - r0][k1][j2]
     double invN;
+    int r0, nr;         // residue block: residues r0 .. r0 + nr - 1
+    int accumulate;     // colbwd: add to the output (blocks after the first)
 };
 
 template <int S1, bool INV, class T>
@@ -79,7 +85,7 @@ __device__ __forceinline__ void split_colfwd_body(const SplitArgs& a, int64_t in
         v[j1] = cmul(cadd(b0, cmul(cr, b1)), ldtw(twR + (int64_t)r * a.S + j));
     }
     dft_small<S1, false>(v);
-    T* w = static_cast<T*>(a.work) + ((inst * a.A + aa) * a.n + r) * (int64_t)a.S;
+    T* w = static_cast<T*>(a.work) + ((inst * a.A + aa) * a.nr + (r - a.r0)) * (int64_t)a.S;
 #pragma unroll
     for (int k1 = 0; k1 < S1; ++k1) {
         const T t = k1 == 0 ? v[0] : cmul(v[k1], ldtw(twS + k1 * a.S2 + j2));
@@ -115,7 +121,7 @@ __device__ __forceinline__ void split_colfwd_multi(const SplitArgs& a, int64_t i
             v[u][j1] = cmul(cadd(b0, cmul(cr, b1)), ldtw(twR + (int64_t)r * a.S + j));
         }
     }
-    T* w = static_cast<T*>(a.work) + ((inst * a.A + aa) * a.n + r) * (int64_t)a.S;
+    T* w = static_cast<T*>(a.work) + ((inst * a.A + aa) * a.nr + (r - a.r0)) * (int64_t)a.S;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         const int j2 = j2base + u * jstep;
@@ -132,12 +138,12 @@ __device__ __forceinline__ void split_colfwd_multi(const SplitArgs& a, int64_t i
 template <class R, int S1, int KIND>
 __global__ void __launch_bounds__(256) split_colfwd(const __grid_constant__ SplitArgs a) {
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t total = a.count * a.A * a.n * (int64_t)a.S2;
+    const int64_t total = a.count * a.A * a.nr * (int64_t)a.S2;
     if (tid >= total) return;
     const int j2 = (int)(tid % a.S2);
     int64_t rest = tid / a.S2;
-    const int r = (int)(rest % a.n);
-    rest /= a.n;
+    const int r = a.r0 + (int)(rest % a.nr);
+    rest /= a.nr;
     const int aa = (int)(rest % a.A);
     split_colfwd_body<R, S1, KIND>(a, rest / a.A, aa, r, j2);
 }
@@ -156,14 +162,14 @@ __device__ __forceinline__ void split_row_body(const SplitArgs& a, int64_t row, 
     static_assert(MultShape<MULT>::B == 1, "single-output mults only");
     const int k1 = (int)(row % a.S1);
     const int64_t rr = row / a.S1;
-    const int r = (int)(rr % a.n);
-    const int64_t inst = rr / a.n;
+    const int rb = (int)(rr % a.nr);   // residue a.r0 + rb
+    const int64_t inst = rr / a.nr;
     const TwGlobal<T> tw{static_cast<const T*>(a.twS2)};
     T* base = static_cast<T*>(a.work);
     T v[A * E];
 #pragma unroll
     for (int aa = 0; aa < A; ++aa) {
-        const T* src = base + ((inst * A + aa) * a.n + r) * (int64_t)a.S + (int64_t)k1 * S2;
+        const T* src = base + ((inst * A + aa) * a.nr + rb) * (int64_t)a.S + (int64_t)k1 * S2;
 #pragma unroll
         for (int e = 0; e < E; ++e) v[aa * E + e] = valid ? src[tau + TT * e] : czero<T>();
     }
@@ -173,7 +179,7 @@ __device__ __forceinline__ void split_row_body(const SplitArgs& a, int64_t row, 
     if (DISCARD && valid) {
 #pragma unroll
         for (int aa = 1; aa < A; ++aa)
-            l2_discard(base + ((inst * A + aa) * a.n + r) * (int64_t)a.S + (int64_t)k1 * S2, (int64_t)S2 * sizeof(T),
+            l2_discard(base + ((inst * A + aa) * a.nr + rb) * (int64_t)a.S + (int64_t)k1 * S2, (int64_t)S2 * sizeof(T),
                        tau, TT);
     }
     T p[E];
@@ -196,7 +202,7 @@ __device__ __forceinline__ void split_row_body(const SplitArgs& a, int64_t row, 
     }
     fft_inverse<S2, E, 1>(p, sm, tw, tau);
     if (!valid) return;
-    T* dst = base + ((inst * A + 0) * a.n + r) * (int64_t)a.S + (int64_t)k1 * S2;
+    T* dst = base + ((inst * A + 0) * a.nr + rb) * (int64_t)a.S + (int64_t)k1 * S2;
 #pragma unroll
     for (int e = 0; e < E; ++e) dst[tau + TT * e] = p[e];
 }
@@ -215,18 +221,26 @@ __global__ void __launch_bounds__(ConvLaunch<S2, E>::MAXT) split_row(const __gri
     const int tau = threadIdx.x - g * TT;
     T* sm = reinterpret_cast<T*>(smem_raw) + (size_t)g * A * Sh::SMEM;
     const int64_t row = (int64_t)blockIdx.x * G + g;
-    const int64_t rows = a.count * a.n * (int64_t)a.S1;
+    const int64_t rows = a.count * a.nr * (int64_t)a.S1;
     split_row_body<R, S2, E, KIND, MULT>(a, row, row < rows, tau, sm);
 }
 
-// Backward column j2 of instance inst; all residues accumulated.
+// Output store of the backward columns: the first residue block stores, the
+// later ones add to what the earlier ones stored.
+template <class T>
+__device__ __forceinline__ void split_store(T* p, T v, int accumulate) {
+    if (accumulate) v = cadd(*p, v);
+    __stcs(p, v);
+}
+
+// Backward column j2 of instance inst; all residues of the block accumulated.
 template <class R, int S1, int KIND, bool COMP>
 __device__ __forceinline__ void split_colbwd_body(const SplitArgs& a, int64_t inst, int j2) {
     using T = cplx<R>;
     constexpr int NB = (KIND == KIND_HERMITIAN) ? 1 : 2;
     const T* twR = static_cast<const T*>(a.twR);
     const T* twS = static_cast<const T*>(a.twS);
-    const T* base = static_cast<const T*>(a.work) + inst * a.A * (int64_t)a.n * a.S;
+    const T* base = static_cast<const T*>(a.work) + inst * a.A * (int64_t)a.nr * a.S;
     R s0[2 * S1], c0[COMP ? 2 * S1 : 1], s1[NB == 2 ? 2 * S1 : 1], c1[(NB == 2 && COMP) ? 2 * S1 : 1];
     R dummy = 0;
 #pragma unroll
@@ -238,13 +252,13 @@ __device__ __forceinline__ void split_colbwd_body(const SplitArgs& a, int64_t in
             if constexpr (COMP) c1[i] = 0;
         }
     }
-    for (int r = 0; r < a.n; ++r) {
+    for (int r = a.r0; r < a.r0 + a.nr; ++r) {
         T cr = ldtw(twR + (int64_t)a.n * a.S + r);
         if constexpr (KIND != KIND_COMPLEX) cr = cconj(cr);
         T v[S1];
 #pragma unroll
         for (int k1 = 0; k1 < S1; ++k1) {
-            const T z = base[(int64_t)r * a.S + (int64_t)k1 * a.S2 + j2];
+            const T z = base[(int64_t)(r - a.r0) * a.S + (int64_t)k1 * a.S2 + j2];
             v[k1] = k1 == 0 ? z : cmulc(z, ldtw(twS + k1 * a.S2 + j2));
         }
         dft_small<S1, true>(v);
@@ -276,13 +290,13 @@ __device__ __forceinline__ void split_colbwd_body(const SplitArgs& a, int64_t in
             o1 = mk<T>(x1 * sc, y1 * sc);
         }
         if constexpr (KIND == KIND_COMPLEX) {
-            if (j < a.L) __stcs(hout + j, o0);
-            if (j + a.S < a.L) __stcs(hout + j + a.S, o1);
+            if (j < a.L) split_store(hout + j, o0, a.accumulate);
+            if (j + a.S < a.L) split_store(hout + j + a.S, o1, a.accumulate);
         } else if constexpr (KIND == KIND_CENTERED) {
-            if (j < a.L - a.H) __stcs(hout + j + a.H, o0);
-            if (j >= a.S - a.H) __stcs(hout + j - a.S + a.H, o1);
+            if (j < a.L - a.H) split_store(hout + j + a.H, o0, a.accumulate);
+            if (j >= a.S - a.H) split_store(hout + j - a.S + a.H, o1, a.accumulate);
         } else {
-            if (j < a.Ls) __stcs(hout + j, o0);
+            if (j < a.Ls) split_store(hout + j, o0, a.accumulate);
         }
     }
 }
@@ -296,7 +310,7 @@ __device__ __forceinline__ void split_colbwd_multi(const SplitArgs& a, int64_t i
     constexpr int NA = 2 * S1;
     const T* twR = static_cast<const T*>(a.twR);
     const T* twS = static_cast<const T*>(a.twS);
-    const T* base = static_cast<const T*>(a.work) + inst * a.A * (int64_t)a.n * a.S;
+    const T* base = static_cast<const T*>(a.work) + inst * a.A * (int64_t)a.nr * a.S;
     R s0[U][NA], c0[U][COMP ? NA : 1], s1[U][NB == 2 ? NA : 1], c1[U][(NB == 2 && COMP) ? NA : 1];
     R dummy = 0;
 #pragma unroll
@@ -310,7 +324,7 @@ __device__ __forceinline__ void split_colbwd_multi(const SplitArgs& a, int64_t i
                 if constexpr (COMP) c1[u][i] = 0;
             }
         }
-    for (int r = 0; r < a.n; ++r) {
+    for (int r = a.r0; r < a.r0 + a.nr; ++r) {
         T cr = ldtw(twR + (int64_t)a.n * a.S + r);
         if constexpr (KIND != KIND_COMPLEX) cr = cconj(cr);
         T v[U][S1];
@@ -318,7 +332,7 @@ __device__ __forceinline__ void split_colbwd_multi(const SplitArgs& a, int64_t i
         for (int u = 0; u < U; ++u)
 #pragma unroll
             for (int k1 = 0; k1 < S1; ++k1)
-                v[u][k1] = base[(int64_t)r * a.S + (int64_t)k1 * a.S2 + j2base + u * jstep];
+                v[u][k1] = base[(int64_t)(r - a.r0) * a.S + (int64_t)k1 * a.S2 + j2base + u * jstep];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int j2 = j2base + u * jstep;
@@ -357,13 +371,13 @@ __device__ __forceinline__ void split_colbwd_multi(const SplitArgs& a, int64_t i
                 o1 = mk<T>(x1 * sc, y1 * sc);
             }
             if constexpr (KIND == KIND_COMPLEX) {
-                if (j < a.L) __stcs(hout + j, o0);
-                if (j + a.S < a.L) __stcs(hout + j + a.S, o1);
+                if (j < a.L) split_store(hout + j, o0, a.accumulate);
+                if (j + a.S < a.L) split_store(hout + j + a.S, o1, a.accumulate);
             } else if constexpr (KIND == KIND_CENTERED) {
-                if (j < a.L - a.H) __stcs(hout + j + a.H, o0);
-                if (j >= a.S - a.H) __stcs(hout + j - a.S + a.H, o1);
+                if (j < a.L - a.H) split_store(hout + j + a.H, o0, a.accumulate);
+                if (j >= a.S - a.H) split_store(hout + j - a.S + a.H, o1, a.accumulate);
             } else {
-                if (j < a.Ls) __stcs(hout + j, o0);
+                if (j < a.Ls) split_store(hout + j, o0, a.accumulate);
             }
         }
     }

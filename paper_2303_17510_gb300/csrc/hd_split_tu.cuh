@@ -15,7 +15,7 @@ cudaError_t run_split(const SplitArgs& a, cudaStream_t st) {
     constexpr int T = S2 / E;
     constexpr int A = MultShape<MULT>::A;
     static_assert(MultShape<MULT>::B == 1, "single-output mults only");
-    const int64_t n1 = a.count * a.A * a.n * (int64_t)S2;
+    const int64_t n1 = a.count * a.A * a.nr * (int64_t)S2;
     if (n1 <= 0) return cudaSuccess;
     split_colfwd<R, S1, KIND><<<(unsigned)((n1 + 255) / 256), 256, 0, st>>>(a);
     cudaError_t e = cudaGetLastError();
@@ -27,7 +27,7 @@ cudaError_t run_split(const SplitArgs& a, cudaStream_t st) {
         e = cudaFuncSetAttribute(rk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    const int64_t rows = a.count * a.n * (int64_t)S1;
+    const int64_t rows = a.count * a.nr * (int64_t)S1;
     rk<<<(unsigned)((rows + G - 1) / G), G * T, smem, st>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

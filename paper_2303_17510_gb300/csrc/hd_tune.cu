@@ -94,7 +94,7 @@ int enumerate_candidates(const hd_desc* d, std::vector<hd_candidate>* out) {
             // identical kernel work (same S, n, variant): keep the smallest p
             bool dup = false;
             for (auto& c : *out) {
-                if (c.S == S && c.n == n && c.E == vars[v].E && c.minb == vars[v].minb) {
+                if (c.S == S && c.n == n && c.E == vars[v].E && c.minb == vars[v].minb && single_group(d->kind, c)) {
                     if (p < c.p) {
                         c.m = m;
                         c.p = p;
@@ -118,6 +118,39 @@ int enumerate_candidates(const hd_desc* d, std::vector<hd_candidate>* out) {
             c.comp = comp ? 1 : 0;
             c.ms = 0;
             out->push_back(c);
+        }
+        // D > 1 residues per pass (Section 6.5) for few convolutions: D residue
+        // groups of one convolution run at once on a thread-block cluster
+        if (d->kind != HD_HERMITIAN && !split_supported(d->dtype, d->kind, d->mult, S, nb)) {
+            for (int ci = 0; ci < 6; ++ci) {
+                const int D = ci < 3 ? 2 : 4, E = 8 >> (ci % 3);
+                if (D > n || !cluster_supported(d->dtype, d->kind, d->mult, S, nb, Ls, D, E)) continue;
+                bool dup = false;
+                for (auto& c : *out) {
+                    if (c.S == S && c.n == n && c.D == D && c.E == E) {
+                        if (p < c.p) {
+                            c.m = m;
+                            c.p = p;
+                            c.q = q;
+                        }
+                        dup = true;
+                        break;
+                    }
+                }
+                if (dup) continue;
+                hd_candidate c;
+                std::memset(&c, 0, sizeof(c));
+                c.m = m;
+                c.p = p;
+                c.q = q;
+                c.D = D;
+                c.S = S;
+                c.n = n;
+                c.E = E;
+                c.minb = 1;
+                c.comp = 0;
+                out->push_back(c);
+            }
         }
     }
     return (int)out->size();
@@ -211,9 +244,11 @@ hd_status hd_autotune(const hd_desc* d, int64_t count, int reps, hd_candidate* o
     const int64_t Ls = d->kind == HD_HERMITIAN ? (d->L[0] + 1) / 2 : d->L[0];
     const size_t esz = d->dtype == HD_F64 ? 16 : 8;
     const size_t bytes = (size_t)count * (size_t)Ls * esz;
-    void* buf[4] = {nullptr, nullptr, nullptr, nullptr};
+    constexpr int kBufs = 3 + kMaxOut;
+    void* buf[kBufs] = {};
     hd_status st = HD_OK;
-    for (int a = 0; a < d->A + d->B && st == HD_OK; ++a) {   // A inputs, B outputs (at most 4)
+    if (d->A + d->B > kBufs) return HD_ERR_INVALID;
+    for (int a = 0; a < d->A + d->B && st == HD_OK; ++a) {   // A inputs, B outputs
         if (cudaMalloc(&buf[a], bytes) != cudaSuccess) st = HD_ERR_NOMEM;
         else if (cudaMemset(buf[a], 0, bytes) != cudaSuccess) st = HD_ERR_CUDA;
     }
@@ -228,7 +263,8 @@ hd_status hd_autotune(const hd_desc* d, int64_t count, int reps, hd_candidate* o
             continue;
         }
         const void* f[3] = {buf[0], buf[1], buf[2]};
-        void* h[2] = {buf[d->A], d->B > 1 ? buf[d->A + 1] : nullptr};
+        void* h[kMaxOut] = {};
+        for (int b = 0; b < d->B && b < kMaxOut; ++b) h[b] = buf[d->A + b];
         t.clear();
         for (int r = 0; r < 2 + reps && st == HD_OK; ++r) {
             cudaEventRecord(e0, 0);
@@ -245,7 +281,7 @@ hd_status hd_autotune(const hd_desc* d, int64_t count, int reps, hd_candidate* o
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < kBufs; ++a)
         if (buf[a]) cudaFree(buf[a]);
     if (st != HD_OK) {
         cudaGetLastError();

@@ -58,6 +58,8 @@ def collect(problems, reps=3, work=1 << 21):
         for c in allc:
             if c["ms"] <= 0:
                 continue
+            if c["D"] > 1 and p["kind"] != "hermitian":   # cluster variants: not selector candidates
+                continue
             X.append(b.selector_features(c, L=p["L"], M=p["M"], A=p["A"], kind=p["kind"], dtype="f32"))
             y.append(math.log(c["ms"] * 1e3 / count))
             pid.append(i)

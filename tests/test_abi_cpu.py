@@ -86,7 +86,7 @@ def test_enumerated_candidates_are_legal(hd, kind, dtype):
                     assert p == want[0] or (p > want[0] and p & (p - 1) == 0)
                 else:
                     assert m >= M
-                key = (S, n, c["E"], c["minb"])
+                key = (S, n, c["E"], c["minb"], c["D"])
                 assert key not in seen
                 seen.add(key)
             # at least one candidate with the paper's own p for the largest legal m
@@ -120,3 +120,52 @@ def test_mult_counts_validated(hd):
     cands = hd.enumerate_candidates(L=20000, M=39999, A=2, B=2)
     assert cands == []
     assert hd.enumerate_candidates(L=4096, M=8191, A=2, B=2)
+
+
+def test_ragged_workload_same_with_library_or_oracle_bounds(hd):
+    """The ragged workload takes its dealiasing bounds from the caller: the
+    library's hd_dealias_bound and the oracle's definition give the same
+    10,000 instances (both are pinned to the paper's bounds elsewhere)."""
+    import inputs
+    from oracle import params
+    a = inputs.ragged_instances(10000, 4, hd.dealias_bound)
+    b = inputs.ragged_instances(10000, 4, params.dealias_bound)
+    assert a == b
+    assert sum(d["clamped"] for d in a) > 0
+    assert all(d["M"] >= params.dealias_bound(d["kind"], d["L"]) for d in a)
+
+
+def test_cluster_candidates_enumerated(hd):
+    """D > 1 residues per pass (one convolution on a thread-block cluster of
+    D x A CTAs) is offered for complex and centered data with n >= D residues
+    and at most 8 CTAs; Hermitian candidates keep D = 2 (residue pairs)."""
+    cs = hd.enumerate_candidates(L=1024, M=2047, dtype="f64")
+    cl = sorted((c["S"], c["n"], c["D"], c["E"]) for c in cs if c["D"] > 1)
+    assert cl == [(512, 4, 2, 2), (512, 4, 2, 4), (512, 4, 2, 8), (512, 4, 4, 2), (512, 4, 4, 4), (512, 4, 4, 8),
+                  (1024, 2, 2, 4), (1024, 2, 2, 8)]
+    for c in hd.enumerate_candidates(L=1000, M=1500, A=3, kind="centered"):
+        assert c["D"] * 3 <= 8 or c["D"] == 1
+        assert c["D"] <= c["n"]
+    assert all(c["D"] == 2 for c in hd.enumerate_candidates(L=1000, M=1500, kind="hermitian") if c["S"] <= 4096)
+    for c in hd.enumerate_candidates(L=20000, M=39999):
+        if c["S"] > 4096:
+            assert c["D"] == 1                            # no cluster form of the split path
+
+
+def test_basdevant3_counts_and_bounds(hd):
+    """The five-output mult (A = 3, B = 5) has the binary dealiasing bounds,
+    is inferred from (A, B) = (3, 5), and is refused with other counts, on the
+    split path and in ragged batches, before any device work."""
+    from oracle import params
+    for kind in ("complex", "centered", "hermitian"):
+        for L in (1, 100, 257):
+            assert hd.dealias_bound(kind, L, "basdevant3") == params.dealias_bound(kind, L, "basdevant3")
+    for A, B in ((2, 5), (3, 4)):
+        with pytest.raises(hd.HdError) as e:
+            hd.Plan(100, 199, A=A, B=B, mult="basdevant3")
+        assert e.value.name == "HD_ERR_INVALID", (A, B)
+    assert hd.enumerate_candidates(L=20000, M=39999, A=3, B=5) == []
+    assert all(c["S"] <= 4096 for c in hd.enumerate_candidates(L=3000, M=5999, A=3, B=5))
+    import ctypes
+    out = ctypes.c_void_p()
+    assert hd.lib.hd_plan_create(ctypes.byref(out), 100, 199, 3, 4, 0, 0, 0, 0) == 1   # HD_ERR_INVALID

@@ -282,3 +282,46 @@ def test_persistent_bulk_copy_variant_matches_plain_kernel(hd):
         got = out[1:].cpu().numpy().reshape(count, L)
     assert np.array_equal(got, plains[0])
     assert hd.device_status() == "HD_OK"     # no bounded wait of the persistent kernels ran out
+
+
+@pytest.mark.parametrize("kind", ["complex", "centered"])
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_cluster_residue_groups(hd, kind, dtype):
+    """D > 1 residues per pass (Section 6.5): one convolution on a cluster of
+    D x A CTAs, residue groups reduced through distributed shared memory.
+    Every enumerated cluster candidate, both mults; FP64 on integer inputs is
+    exact after rint, FP32 within the bound; the sums are deterministic."""
+    ran = 0
+    for mult, A in (("product", 2), ("sum_pairs3", 3)):
+        for L in (5, 100, 1000, 1024, 3000):
+            fs = make_inputs(kind, L, A, 3, 500 + L, integer=(dtype == "f64"))
+            ref = direct.conv1d_batch(fs, kind, mult)
+            M = params.dealias_bound(kind, L, mult) + 1
+            for c in hd.enumerate_candidates(L=L, M=M, A=A, kind=kind, dtype=dtype):
+                if c["D"] <= 1:
+                    continue
+                assert c["D"] <= c["n"] and c["D"] * A <= 8
+                with hd.Plan(L, M, A=A, kind=kind, dtype=dtype, candidate=c) as plan:
+                    got = run_conv(hd, plan, fs)
+                    check(got, ref, dtype, dtype == "f64", (kind, dtype, mult, L, c))
+                    assert np.array_equal(run_conv(hd, plan, fs), got)
+                ran += 1
+    assert ran >= 8
+
+
+def test_cluster_explicit_D_and_refusals(hd):
+    """Plans asking for D residue groups directly: the single FP64 convolution
+    of L = 1024, M = 2047 with m = 512 (n = 4 residues) at D = 2 and 4; D
+    beyond the residue count or the cluster size is refused."""
+    L, M = 1024, 2047
+    fs = make_inputs("complex", L, 2, 1, 77, integer=True)
+    ref = direct.conv1d_batch(fs, "complex")
+    for D in (2, 4):
+        with hd.Plan(L, M, m=512, D=D, dtype="f64") as plan:
+            assert plan.axis_params(0)["D"] == D and plan.axis_params(0)["n"] == 4
+            check(run_conv(hd, plan, [f[0] for f in fs]), ref[0], "f64", True, D)
+    for kw in (dict(m=512, D=8), dict(m=1024, D=4), dict(m=512, D=4, A=3)):
+        A = kw.pop("A", 2)
+        with pytest.raises(hd.HdError) as e:
+            hd.Plan(L, 3 * L if A == 3 else M, A=A, dtype="f64", **kw)
+        assert e.value.name == "HD_ERR_UNSUPPORTED", kw

@@ -98,7 +98,7 @@ def test_selector_plans_ragged_sample_100x_faster_than_search(hd):
     import torch
     import inputs
     from paper_2303_17510_gb300 import selector
-    descs = inputs.ragged_instances(2000, 13)
+    descs = inputs.ragged_instances(2000, 13, hd.dealias_bound)
     tot = sum(d["L"] for d in descs)
     base = [torch.from_numpy(inputs.uniform_complex(tot, 80 + a, dtype=np.complex64)).cuda() for a in range(3)]
     out = torch.empty(tot, dtype=torch.complex64, device="cuda")

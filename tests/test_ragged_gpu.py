@@ -39,7 +39,7 @@ def oracle_of(d, xs):
 
 def test_ragged_matches_oracle_and_replays(hd):
     import torch
-    descs = inputs.ragged_instances(240, 11, L_lo=64, L_hi=24000)
+    descs = inputs.ragged_instances(240, 11, hd.dealias_bound, L_lo=64, L_hi=24000)
     fs, hs, host = make_batch(descs, 100)
     with hd.RaggedPlan(descs) as plan:
         kinds = set()
@@ -108,7 +108,7 @@ def test_ragged_full_size(hd):
     sum; nine more instances (shortest, median, longest L) on 64 points."""
     import concurrent.futures as cf
     import torch
-    descs = inputs.ragged_instances(10000, 4)
+    descs = inputs.ragged_instances(10000, 4, hd.dealias_bound)
     tot = sum(d["L"] for d in descs)
     base = [torch.from_numpy(inputs.uniform_complex(tot, 50 + a, dtype=np.complex64)).cuda() for a in range(3)]
     out = torch.empty(tot, dtype=torch.complex64, device="cuda")

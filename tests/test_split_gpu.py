@@ -69,3 +69,34 @@ def test_split_chunking_and_inplace(hd):
         torch.cuda.synchronize()
         got = d[0].cpu().numpy()[ref_idx]
         assert rel_l2_rows(got, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("kind,L,A", [("complex", 9000, 2), ("centered", 20000, 2), ("hermitian", 30001, 2),
+                                      ("complex", 6000, 3)])
+def test_split_residue_blocks(hd, kind, L, A):
+    """D residues per pass on the split path (Section 6.5): the residues run in
+    blocks of D whose contributions are added into the output, so the work
+    buffer holds A D S values per instance instead of A n S.  Every block size
+    gives the oracle's result; writing over an input is refused."""
+    import torch
+    M = 2 * params.dealias_bound(kind, L) + 11          # more residues than the tightest padding
+    mult = "product" if A == 2 else "sum_pairs3"
+    fs = make_inputs(kind, L, A, 3, 900 + L)
+    ref = cdirect.conv1d_batch(fs, L, kind, mult)
+    c = max(split_cands(hd, L=L, M=M, A=A, kind=kind), key=lambda c: c["n"])
+    assert c["n"] >= 3, c
+    with hd.Plan(L, M, A=A, kind=kind, candidate=c) as plan:
+        one = plan.params()["scratch_bytes"]
+    for D in (2, c["n"] - 1):
+        with hd.Plan(L, M, A=A, kind=kind, m=c["m"], p=c["p"], q=c["q"], D=D) as plan:
+            ax = plan.axis_params(0)
+            assert (ax["S"], ax["n"], ax["D"]) == (c["S"], c["n"], D)
+            per_block = A * D * c["S"] * 8
+            assert plan.params()["scratch_bytes"] % per_block == 0
+            assert plan.params()["scratch_bytes"] // per_block >= one // (A * c["n"] * c["S"] * 8)
+            got = run_conv(hd, plan, fs)
+            assert rel_l2_rows(got, ref) <= 1e-5, (kind, D)
+            d = [torch.from_numpy(f.astype(np.complex64)).cuda() for f in fs]
+            with pytest.raises(hd.HdError) as e:
+                plan.convolve_batched(d, d[0], 3, fs[0].shape[1])
+            assert e.value.name == "HD_ERR_INVALID"

@@ -120,3 +120,29 @@ def test_noalloc_rejects_oversize_and_other_plans(hd):
         assert b.STATUS[_call(b, plan, 1, [y, y], y, 1024)] == "HD_ERR_UNSUPPORTED"
     with hd.RaggedPlan([dict(L=9000, M=17999, A=2, kind="complex")]) as plan:
         assert b.STATUS[_call(b, plan, 1, [y, y], y, 1024)] == "HD_ERR_INVALID"
+
+
+def test_noalloc_residue_blocks_lift_the_size_limit(hd):
+    """An instance whose work buffer for all residues exceeds the fixed buffer
+    (A n S values) runs when its plan processes the residues in blocks of D
+    (A D S values per instance): same result as hd_convolve_batched on the same
+    plan, bit for bit, and the FP32 bound against the oracle on sampled points."""
+    import torch
+    from paper_2303_17510_gb300 import _binding as b
+
+    L, M = 60000, 33 * 65536
+    cand = [c for c in hd.enumerate_candidates(L=L, M=M) if c["S"] == 65536][0]
+    assert 2 * cand["n"] * cand["S"] * 8 > NOALLOC_BYTES
+    host = [inputs.uniform_complex((1, L), 990 + a, dtype=np.complex64) for a in range(2)]
+    f = [torch.from_numpy(x[0]).cuda() for x in host]
+    with hd.Plan(L, M, m=cand["m"], p=cand["p"], q=cand["q"], D=16) as plan:
+        assert 2 * 16 * cand["S"] * 8 <= NOALLOC_BYTES
+        ref = torch.empty_like(f[0])
+        plan.convolve_batched(f, ref, 1, L)
+        out = torch.full_like(f[0], float("nan"))
+        assert b.STATUS[_call(b, plan, 1, f, out, L)] == "HD_OK"
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref)
+    idx = np.unique(np.linspace(0, L - 1, 48).astype(np.int64))
+    want = cdirect.conv1d_points([x[0].astype(np.complex128) for x in host], L, idx, "complex")
+    assert _rel_l2(out.cpu().numpy()[idx].astype(np.complex128), want) <= F32_TOL
