@@ -140,6 +140,22 @@ def conv_flops(S, n, A=2, B=1):
     return n * (A + B) * fft_flops(S)
 
 
+def conv_flops_nd(axes, stored, A, B, hermitian):
+    """FFT flops of one N-D convolution by the decomposition of Section 5, in
+    the convention of conv_flops: on outer axis k, (A + B) n_k transforms of
+    size S_k per column for every transformed instance of the axes before it;
+    on the innermost axis, (A + B) transforms per residue (Hermitian residues
+    in pairs, one FFT per pair) for every row the outer axes produce."""
+    fl, inst = 0.0, 1
+    for k, ax in enumerate(axes[:-1]):
+        cols = int(np.prod(stored[k + 1:]))
+        fl += inst * cols * (A + B) * ax["n"] * fft_flops(ax["S"])
+        inst *= ax["n"] * ax["S"]
+    ax = axes[-1]
+    groups = (ax["n"] + 1) // 2 if hermitian else ax["n"]
+    return fl + inst * (A + B) * groups * fft_flops(ax["S"])
+
+
 # ----------------------------------------------------------------------------- CPU oracle rates
 
 def oracle_rate_1d(budget_s, L, kinds, integer=False):
@@ -753,6 +769,7 @@ def run_2d(args, ctx, hd):
                      "f32": {k: v for k, v in res["f32"].items() if k != "clocks"},
                      "f64": {k: v for k, v in res["f64"].items() if k != "clocks"}})
     out.update({"roofline": roofline(3 * L * L * 8, ms, read_traffic("2d"), "2d plan (all kernels of one convolution)"),
+                "alu": alu(conv_flops_nd(res["f32"]["axes"], [L, L], 2, 1, False), ms, res["f32"]["clocks"]),
                 "accuracy": {"rel_l2_sampled": res["f32"]["rel_l2_sampled"], "points": len(pts)},
                 "baselines": {"fp64_hybrid": {"value": 1e3 / res["f64"]["ms"], "unit": "conv/s",
                                               "rel_l2_sampled": res["f64"]["rel_l2_sampled"]},
@@ -850,6 +867,7 @@ def run_ns2d(args, ctx, hd):
                      "scratch_bytes": scratch,
                      "l2": "4 input/output sets of 64 MiB rotated over the timed calls (256 MiB > L2)"})
     out.update({"roofline": roofline(4 * L * H * 8, ms, read_traffic("ns2d"), "ns2d plan (all kernels)"),
+                "alu": alu(conv_flops_nd(axes, [L, H], 2, 2, True), ms, clocks),
                 "accuracy": {"rel_l2_sampled": acc, "points": len(pts)},
                 "baselines": {"cufft_f32_explicit_3072^2_real": {"value": 1e3 / cu, "unit": "conv/s", "ms": cu}},
                 # one convolution: outer-axis forward, the inner batch of rows, outer-axis backward
@@ -933,6 +951,7 @@ def run_3d(args, ctx, hd):
                      "scratch_bytes": plan.params()["scratch_bytes"],
                      "l2": "inputs+outputs 96 MiB; work buffers larger than L2"})
     out.update({"roofline": roofline(3 * L * L * (L // 2) * 8, ms, read_traffic("3d"), "3d plan (all kernels)"),
+                "alu": alu(conv_flops_nd(axes, [L, L, L // 2], 2, 1, True), ms, clocks),
                 "accuracy": {"rel_l2_sampled": acc, "points": len(pts)},
                 "variants": {"cost_model_params": {"ms": ms_cm, "axes": axes_cm},
                              "compensated_sums": {"ms": ms_comp, "rel_l2_sampled": acc_comp}},
@@ -1047,6 +1066,7 @@ def run_ragged(args, ctx, hd):
                 "selector_vs_exhaustive": (res["selector"] / res["exhaustive"]) if "exhaustive" in res else None,
                 "selector_vs_cost_model": res["selector"] / res["cost_model"],
                 "roofline": roofline(bytes_, ms, read_traffic("ragged"), "ragged_kernel"),
+                "alu": alu(sum(conv_flops(c["S"], c["n"], d["A"], 1) for c, d in zip(sel, descs)), ms, clocks),
                 "accuracy": {"rel_l2_sampled_max": max(errs), "instances": len(pick)},
                 "e2e": e2e, "gpu_launches": reps, "clocks": clocks})
     if ctx.rank == 0 and not args.no_cpu_baseline:

@@ -73,12 +73,14 @@ __global__ void __launch_bounds__(ColShape<S, E>::THREADS) col_forward(const __g
         b0[e] = czero<T>();
         b1[e] = czero<T>();
         if (valid) {
+            // read once: streaming loads, so the column data does not evict the
+            // twiddle tables from L1
             if constexpr (KIND == KIND_COMPLEX) {
-                if (j < a.L) b0[e] = f[(int64_t)j * a.pitch];
-                if (j + S < a.L) b1[e] = f[(int64_t)(j + S) * a.pitch];
+                if (j < a.L) b0[e] = ld_in<true>(f, (int64_t)j * a.pitch);
+                if (j + S < a.L) b1[e] = ld_in<true>(f, (int64_t)(j + S) * a.pitch);
             } else {
-                if (j < a.L - a.H) b0[e] = f[(int64_t)(j + a.H) * a.pitch];
-                if (j >= S - a.H) b1[e] = f[(int64_t)(j - S + a.H) * a.pitch];
+                if (j < a.L - a.H) b0[e] = ld_in<true>(f, (int64_t)(j + a.H) * a.pitch);
+                if (j >= S - a.H) b1[e] = ld_in<true>(f, (int64_t)(j - S + a.H) * a.pitch);
             }
         }
     }
@@ -138,7 +140,7 @@ __global__ void __launch_bounds__(ColShape<S, E>::THREADS) col_backward(const __
                      (valid ? col : 0);
         T v[E];
 #pragma unroll
-        for (int e = 0; e < E; ++e) v[e] = valid ? g[(int64_t)(tau + TT * e) * a.ncols] : czero<T>();
+        for (int e = 0; e < E; ++e) v[e] = valid ? ld_in<true>(g, (int64_t)(tau + TT * e) * a.ncols) : czero<T>();
         fft_inverse<S, E, 1, TY>(v, sm, tw, tau);
         const bool r0 = r == 0;   // unit twists
 #pragma unroll

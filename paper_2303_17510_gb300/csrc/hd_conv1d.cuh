@@ -163,6 +163,11 @@ __device__ __forceinline__ T ld_in(const T* f, int i) {
     if constexpr (STREAM) return __ldcs(f + i);
     else return f[i];
 }
+template <bool STREAM, class T>
+__device__ __forceinline__ T ld_in(const T* f, int64_t i) {
+    if constexpr (STREAM) return __ldcs(f + i);
+    else return f[i];
+}
 
 // Stored input value(s) folded to transform slot j (see header comment).
 // Returns block-0 and block-1 values (block 1 is conj-mirrored for Hermitian).
