@@ -107,6 +107,7 @@ struct hd_plan {
     void* scratch;     // split-path work buffer (chunk * A * n * S values)
     void* work[2];     // N-D: work buffer of each outer axis level
     int64_t inst_cap;  // N-D: outer instances per pass through the levels
+    int64_t level_chunk[2];   // N-D: instances of outer level k handled per pass (its work buffer's size)
     hd::RaggedData* ragged;   // ragged batch plans (hd_ragged.cu)
     int device;
     hd_status sticky;

@@ -197,3 +197,27 @@ def test_3d_hermitian_full_size(hd):
     want = direct.convnd_points(f64, kinds, pts)
     assert np.allclose(full[tuple(pts.T)], want, rtol=1e-12, atol=1e-12 * np.max(np.abs(want)))
     point_checks(got[tuple(pts.T)], want, Ntot, float(np.sqrt(np.mean(np.abs(full) ** 2))))
+
+
+@pytest.mark.parametrize("kind", ["complex", "hermitian"])
+def test_3d_middle_level_chunks(hd, monkeypatch, kind):
+    """The middle axis of a 3D plan can run its independent instances (the
+    outer axis's transformed slices) in chunks whose work buffer stays in L2
+    (HD_ND_CHUNK_MB; off by default): a small chunk limit gives the same
+    result, bit for bit, as no limit, and the FP32 bound against the FP64
+    explicit zero-padded FFT convolution."""
+    L = 40
+    if kind == "hermitian":
+        fs = [inputs.hermitian_3d(L, 770 + a, dtype=np.complex64) for a in range(2)]
+        kinds, Ms = ("centered", "centered", "hermitian"), [60, 60, 60]
+    else:
+        fs = [inputs.uniform_complex((L, L, L), 770 + a, dtype=np.complex64) for a in range(2)]
+        kinds, Ms = ("complex",) * 3, [79, 79, 79]
+    outs = []
+    for mb in ("1", ""):
+        monkeypatch.setenv("HD_ND_CHUNK_MB", mb)
+        with hd.Plan([L, L, L], Ms, kind=kind) as plan:
+            outs.append(run_nd(hd, plan, fs, "f32"))
+    assert np.array_equal(outs[0], outs[1])
+    want = explicit.convnd_explicit([f.astype(np.complex128) for f in fs], kinds, Ms)
+    assert rel_l2(outs[0], want) <= 1e-5
