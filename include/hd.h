@@ -172,6 +172,26 @@ hd_status hd_convolve(const hd_plan* plan, const void* const* f, void* const* h,
 hd_status hd_convolve_batched(const hd_plan* plan, int64_t count, const void* const* f, void* const* h,
                               int64_t batch_stride, void* stream);
 
+/* Partial convolution over a range of residues (Section 2.2: the transformed
+ * residues are independent and each one's backward transform is added into the
+ * output, so the output is the sum of the n residue contributions).  Writes to
+ * h[b] the sum of the contributions of residues r_begin <= r < r_end of the
+ * plan's outermost axis (for N-D plans, the residues of axis 0; every residue
+ * of the inner axes), divided by q m like the whole result.  Summing the
+ * outputs of calls whose ranges partition [0, n) gives hd_convolve_batched's
+ * result up to rounding: this is how a convolution is split across GPUs, each
+ * taking a residue range and the partial outputs summed by one reduction.
+ * n is hd_plan_get_axis_params(plan, 0, ...)'s n.  Hermitian 1D plans transform
+ * residues in pairs (r, r + 1) starting at r_begin.
+ *   - 0 <= r_begin <= r_end <= n, else HD_ERR_INVALID; r_begin = r_end writes
+ *     zeros to the outputs.
+ *   - Outputs must not overlap the inputs when the range is a proper part of
+ *     [0, n) (HD_ERR_INVALID where the library can tell); ragged plans are
+ *     HD_ERR_INVALID.
+ * Other arguments and results are those of hd_convolve_batched. */
+hd_status hd_convolve_residues(const hd_plan* plan, int64_t r_begin, int64_t r_end, int64_t count,
+                               const void* const* f, void* const* h, int64_t batch_stride, void* stream);
+
 /* Parameters actually used (per axis 0): m, p, q, D and the plan's device
  * scratch bytes.  Any output pointer may be NULL. */
 hd_status hd_plan_get_params(const hd_plan* plan, int64_t* m, int64_t* p, int64_t* q, int* D,
@@ -374,9 +394,11 @@ hd_status hd_convolve_batched_noalloc(const hd_plan* plan, int64_t count, const 
 
 /* Synchronizes the current device and reports whether any persistent
  * batched kernel launched on it since the last call had a bounded wait on its
- * staging copies run out (HD_ERR_TIMEOUT; the affected batch elements are not
- * computed), HD_ERR_CUDA on a device error, HD_OK otherwise.  Clears the
- * report.  (No counterpart in the paper: the persistent kernels stage their
+ * staging copies run out (HD_ERR_TIMEOUT), HD_ERR_CUDA on a device error,
+ * HD_OK otherwise.  Clears the report.  After HD_ERR_TIMEOUT the outputs of
+ * every batched call since the last report are undefined (a CTA that gave up
+ * leaves its remaining batch elements uncomputed, and waits once more, with the
+ * same limit, for its copies in flight before it exits).  (No counterpart in the paper: the persistent kernels stage their
  * inputs with asynchronous bulk copies whose completion they wait for with a
  * time limit.) */
 hd_status hd_device_status(void);

@@ -22,9 +22,13 @@ Modules
               (Eq. forStan, Eq. centDFT, Eq. wHerDef, Section 6.1-6.2).
   steps    -- the paper's residue-at-a-time algorithm (Alg. convolve/convolveX
               with forward1/2/Inner, centered and Hermitian variants) in the
-              paper's order, with an FFT library call as the size-m FFT step.
+              paper's order, with an FFT library call as the size-m FFT step;
+              optionally over a residue range only (the partial sum one share
+              of a residue-split convolution computes, Section 2.2).
   explicit -- explicit zero-padded FFT convolution (the paper's comparison
-              method, Section 7) with numpy's FFT as the FFT step.
+              method, Section 7) with numpy's FFT as the FFT step; optionally
+              with the product spectrum restricted to the frequencies of a
+              residue range on axis 0 (pins the residue partial sums).
   cdirect  -- ctypes wrapper of direct_conv.c, the same definition in plain C
               (multithreaded over instances) for large samples and CPU timing.
   mlp      -- FP64 reference of the parameter-selector MLP (forward, backward,

@@ -17,8 +17,16 @@ import numpy as np
 from .direct import MULT_TERMS, hermitian_expand_nd
 
 
-def convnd_explicit(fs, kinds, Ns, mult="product") -> np.ndarray:
-    """N-D convolution by explicit padding to sizes Ns (one per axis)."""
+def convnd_explicit(fs, kinds, Ns, mult="product", residues=None) -> np.ndarray:
+    """N-D convolution by explicit padding to sizes Ns (one per axis).
+
+    residues = (n, r_begin, r_end): only the frequencies k of axis 0 with
+    k mod n in [r_begin, r_end) enter the inverse transform -- the part of the
+    convolution that residues r_begin <= r < r_end of a hybrid plan with n
+    residues on axis 0 compute (Section 2.2: residue r holds the padded
+    frequencies q l + r, or q l + u n + r for p > 2, all of them = r mod n;
+    frequency k in the paper's positive-exponent convention is numpy's bin
+    -k mod N).  N[0] must be a multiple of n."""
     fs = [np.asarray(f, dtype=np.complex128) for f in fs]
     herm = kinds[-1] == "hermitian"
     if herm:
@@ -41,8 +49,16 @@ def convnd_explicit(fs, kinds, Ns, mult="product") -> np.ndarray:
     out_lo = lo[:-1] + [0] if herm else lo
     out_shape = fs[0].shape
     idx = np.ix_(*[np.mod(np.arange(out_shape[a]) + out_lo[a], Ns[a]) for a in axes])
+    keep = None
+    if residues is not None:
+        n, r0, r1 = residues
+        assert Ns[0] % n == 0
+        k = np.mod(-np.arange(Ns[0]), Ns[0])   # paper frequency of numpy bin j along axis 0
+        keep = ((k % n >= r0) & (k % n < r1)).reshape((-1,) + (1,) * (len(kinds) - 1))
     outs = []
     for t in terms:   # mult, pointwise on the padded spectra
         spec = sum(c * padded[i] * padded[j] for i, j, c in t)
+        if keep is not None:
+            spec = np.where(keep, spec, 0)
         outs.append(np.fft.ifftn(spec, axes=axes)[idx])
     return outs[0] if len(outs) == 1 else np.stack(outs)

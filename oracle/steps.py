@@ -276,15 +276,27 @@ def _outputs(h):
     return h[0] if h.shape[0] == 1 else h
 
 
-def convolve(fs, L, M, m, mult="product", p=None, q=None):
-    """Alg. convolve: complex 1D convolution, one residue at a time."""
+def _residue_range(n, residues):
+    """Residues r_begin <= r < r_end summed (all n by default): the residue
+    contributions are independent and add up (Section 2.2), so a subset gives
+    the partial sum that one share of a residue-split convolution computes."""
+    if residues is None:
+        return range(n)
+    r0, r1 = residues
+    assert 0 <= r0 <= r1 <= n
+    return range(r0, r1)
+
+
+def convolve(fs, L, M, m, mult="product", p=None, q=None, residues=None):
+    """Alg. convolve: complex 1D convolution, one residue at a time
+    (residues = (r_begin, r_end): that part of the residue sum only)."""
     if p is None:
         p, q, n = derive("complex", L, M, m)
     else:
         n = q if p <= 2 else q // p
     fs = [np.asarray(f, dtype=np.complex128) for f in fs]
-    h = None
-    for r in range(n):
+    h = np.zeros((len(_mult([np.zeros(1)] * len(fs), mult)), L), dtype=np.complex128)
+    for r in _residue_range(n, residues):
         if p == 1:
             Fs = [forward1(f, L, m, q, r) for f in fs]
             back = lambda F: backward1(F, L, m, q, r)
@@ -295,19 +307,19 @@ def convolve(fs, L, M, m, mult="product", p=None, q=None):
             Fs = [forwardInner(f, L, m, p, q, n, r) for f in fs]
             back = lambda F: backwardInner(F, L, m, p, q, n, r)
         Hs = _mult(Fs, mult)
-        if h is None:
-            h = np.zeros((len(Hs), L), dtype=np.complex128)
         _accumulate(h, Hs, back)
     return _outputs(h) / (q * m)
 
 
-def convolveX(fs, L, M, m, kind="centered", mult="product"):
-    """Alg. convolveX: centered (X = C) or Hermitian (X = H) 1D convolution."""
+def convolveX(fs, L, M, m, kind="centered", mult="product", residues=None):
+    """Alg. convolveX: centered (X = C) or Hermitian (X = H) 1D convolution
+    (residues as in convolve)."""
     p, q, n = derive(kind, L, M, m)
     fs = [np.asarray(f, dtype=np.complex128) for f in fs]
+    B = len(_mult([np.zeros(1)] * len(fs), mult))
     if kind == "centered":
-        h = None
-        for r in range(n):
+        h = np.zeros((B, L), dtype=np.complex128)
+        for r in _residue_range(n, residues):
             if p == 2:
                 Fs = [forward2C(f, L, m, q, r) for f in fs]
                 back = lambda F: backward2C(F, L, m, q, r)
@@ -315,14 +327,12 @@ def convolveX(fs, L, M, m, kind="centered", mult="product"):
                 Fs = [forwardInnerC(f, L, m, p, q, n, r) for f in fs]
                 back = lambda F: backwardInnerC(F, L, m, p, q, n, r)
             Hs = _mult(Fs, mult)
-            if h is None:
-                h = np.zeros((len(Hs), L), dtype=np.complex128)
             _accumulate(h, Hs, back)
         return _outputs(h) / (q * m)
     if kind == "hermitian":
         Hc = (L + 1) // 2
-        h = None
-        for r in range(n):
+        h = np.zeros((B, Hc), dtype=np.complex128)
+        for r in _residue_range(n, residues):
             if p == 2:
                 Fs = [forward2H(f, L, m, q, r) for f in fs]
                 back = lambda F: backward2H(F, L, m, q, r)
@@ -330,8 +340,6 @@ def convolveX(fs, L, M, m, kind="centered", mult="product"):
                 Fs = [forwardInnerH(f, L, m, p, q, n, r) for f in fs]
                 back = lambda F: backwardInnerH(F, L, m, p, q, n, r)
             Hs = _mult(Fs, mult)
-            if h is None:
-                h = np.zeros((len(Hs), Hc), dtype=np.complex128)
             _accumulate(h, Hs, back)
         return _outputs(h) / (q * m)
     raise ValueError(kind)

@@ -81,6 +81,8 @@ _sig("hd_plan_create", ctypes.c_int, [ctypes.POINTER(_vp), _i64, _i64, ctypes.c_
 _sig("hd_plan_create_ex", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(hd_desc)])
 _sig("hd_convolve", ctypes.c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp])
 _sig("hd_convolve_batched", ctypes.c_int, [_vp, _i64, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i64, _vp])
+_sig("hd_convolve_residues", ctypes.c_int, [_vp, _i64, _i64, _i64, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i64,
+                                            _vp])
 _sig("hd_plan_get_params", ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64),
                                           ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_size_t)])
 _sig("hd_forward_residue", ctypes.c_int, [_vp, _vp, _i64, _vp, _vp])
@@ -287,6 +289,20 @@ class Plan:
         ha = (_vp * self.B)(*[_ptr(h)] if not isinstance(h, (list, tuple)) else [_ptr(x) for x in h])
         _check(lib.hd_convolve_batched(self._h, int(count), fa, ha, int(batch_stride), _stream(stream)),
                "hd_convolve_batched")
+
+    @property
+    def residues(self) -> int:
+        """n: the residue count of the outermost axis (the range of convolve_residues)."""
+        return self.axis_params(0)["n"]
+
+    def convolve_residues(self, fs, h, r_begin, r_end, count=1, batch_stride=0, stream=None):
+        """Partial sums over residues r_begin <= r < r_end of the outermost axis
+        (hd_convolve_residues); over a partition of [0, n) they add up to the
+        convolution."""
+        fa = (_vp * self.A)(*[_ptr(x) for x in fs])
+        ha = (_vp * self.B)(*[_ptr(h)] if not isinstance(h, (list, tuple)) else [_ptr(x) for x in h])
+        _check(lib.hd_convolve_residues(self._h, int(r_begin), int(r_end), int(count), fa, ha, int(batch_stride),
+                                        _stream(stream)), "hd_convolve_residues")
 
     def convolve_batched_noalloc(self, fs, h, count, batch_stride, stream=None):
         """As convolve_batched, over the library's fixed work buffer (no device allocation)."""

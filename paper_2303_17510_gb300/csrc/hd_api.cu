@@ -436,6 +436,42 @@ hd_status hd_convolve_batched(const hd_plan* plan, int64_t count, const void* co
     return hd::plan_execute(const_cast<hd_plan*>(plan), count, f, h, batch_stride, (cudaStream_t)stream);
 }
 
+hd_status hd_convolve_residues(const hd_plan* plan, int64_t r_begin, int64_t r_end, int64_t count,
+                               const void* const* f, void* const* h, int64_t batch_stride, void* stream) {
+    if (!plan || !f || !h || count < 0) return HD_ERR_INVALID;
+    if (plan->ragged) return HD_ERR_INVALID;
+    if (plan->sticky != HD_OK) return plan->sticky;
+    const int64_t n = plan->ax[0].n;
+    if (r_begin < 0 || r_end < r_begin || r_end > n) return HD_ERR_INVALID;
+    if (count == 0) return HD_OK;
+    for (int a = 0; a < plan->A; ++a)
+        if (!f[a]) return HD_ERR_INVALID;
+    for (int b = 0; b < plan->B; ++b)
+        if (!h[b]) return HD_ERR_INVALID;
+    if (count > 1 && batch_stride < plan->instance_elems) return HD_ERR_INVALID;
+    const bool partial = r_begin > 0 || r_end < n;
+    if (partial)
+        for (int a = 0; a < plan->A; ++a)
+            for (int b = 0; b < plan->B; ++b)
+                if (f[a] == h[b]) return HD_ERR_INVALID;
+    if (r_begin == r_end) {
+        // no residue: the partial sum is zero
+        hd::DeviceGuard g(plan->device);
+        const size_t esz = plan->dtype == HD_F64 ? 16 : 8;
+        const int64_t pitch = count > 1 ? batch_stride : plan->instance_elems;
+        for (int b = 0; b < plan->B; ++b) {
+            if (cudaMemset2DAsync(h[b], (size_t)pitch * esz, 0, (size_t)plan->instance_elems * esz, (size_t)count,
+                                  (cudaStream_t)stream) != cudaSuccess) {
+                cudaGetLastError();
+                return HD_ERR_CUDA;
+            }
+        }
+        return HD_OK;
+    }
+    return hd::plan_execute_range(const_cast<hd_plan*>(plan), count, f, h, batch_stride, r_begin, r_end,
+                                  (cudaStream_t)stream);
+}
+
 hd_status hd_forward_residue(const hd_plan* plan, const void* f, int64_t r, void* outp, void* stream) {
     if (!plan || !f || !outp) return HD_ERR_INVALID;
     if (plan->ndim != 1 || plan->ragged) return HD_ERR_INVALID;

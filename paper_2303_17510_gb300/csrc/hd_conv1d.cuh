@@ -41,6 +41,16 @@
 
 #include "hd_fft.cuh"
 
+#ifndef HD_TWP
+#define HD_TWP 0
+#endif
+#ifndef HD_STAGGER
+#define HD_STAGGER 0
+#endif
+#ifndef HD_TWF
+#define HD_TWF 0
+#endif
+
 namespace hd {
 
 enum { KIND_COMPLEX = 0, KIND_CENTERED = 1, KIND_HERMITIAN = 2 };
@@ -133,12 +143,28 @@ struct ConvArgs {
     const void* twN;    // residue twists: zeta_N^{r j} at r S + j (r < n, j < S), then zeta_N^{r S} at n S + r
     double invN;        // 1 / N
     int* err;           // persistent kernel: set to 1 when a bounded wait runs out (may be null)
+    int r_begin, r_end; // residues summed: r_begin <= r < r_end (0, n for the whole convolution);
+                        // Hermitian pairs start at r_begin
 };
 
 template <bool B>
 struct BoolTag {
     static constexpr bool value = B;
 };
+
+// Twist zeta_N^{r j} of slot j = tau + TT e of residue row twr (= twN + r S):
+// the table entry, or (HD_TWF) the product of tb = zeta_N^{r tau} (one read per
+// thread) and zeta_N^{r TT e} (the row's entry TT e, the same for every thread
+// of the CTA: a broadcast read of E entries that stay in L1).
+template <int TT, class T>
+__device__ __forceinline__ T twist_at(const T* twr, T tb, int tau, int e) {
+#if HD_TWF
+    return e == 0 ? tb : cmul(tb, ldtw(twr + TT * e));
+#else
+    (void)tb;
+    return ldtw(twr + tau + TT * e);
+#endif
+}
 
 // Residue-sum accumulation.  COMP: TwoSum compensated s + c += x (FP32 path);
 // otherwise a plain sum.
@@ -224,7 +250,11 @@ __device__ __forceinline__ void conv1d_body(const ConvArgs& a, int64_t inst, boo
     constexpr bool OSM = MultShape<MULT>::OUT_SMEM;
     constexpr int BR = OSM ? 1 : B;   // outputs whose residue sums live in registers
     const T* twN = static_cast<const T*>(a.twN);
+#if HD_TWP
+    const TwGlobalProducts<T> twS{static_cast<const T*>(a.twS)};
+#else
     const TwGlobal<T> twS{static_cast<const T*>(a.twS)};
+#endif
     // OUT_SMEM: residue sums of output b, block nb at acc[(b NB + nb) S + j], each
     // entry read and written only by the thread that owns slot j
     T* acc = sm + MultShape<MULT>::NX * Sh::SMEM;
@@ -274,11 +304,12 @@ __device__ __forceinline__ void conv1d_body(const ConvArgs& a, int64_t inst, boo
             const T* twr = twN + (int64_t)r * S;        // zeta_N^{r j}, j < S
             T cr = R0 ? mk<T>(1, 0) : ldtw(twN + (int64_t)a.n * S + r);    // zeta_N^{r S}
             if constexpr (KIND == KIND_CENTERED) cr = cconj(cr);
+            const T tb = R0 ? mk<T>(1, 0) : ldtw(twr + tau);                 // zeta_N^{r tau}
             T v[A * E];
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const int j = tau + TT * e;
-                const T tw = R0 ? mk<T>(1, 0) : ldtw(twr + j);
+                const T tw = R0 ? mk<T>(1, 0) : twist_at<TT>(twr, tb, tau, e);
 #pragma unroll
                 for (int aa = 0; aa < A; ++aa) {
                     if constexpr (KIND == KIND_COMPLEX && NB == 1) {
@@ -293,12 +324,16 @@ __device__ __forceinline__ void conv1d_body(const ConvArgs& a, int64_t inst, boo
                     }
                 }
             }
-            fft_forward<S, E, A>(v, sm, twS, tau);
-            if (r == a.n - 1) consumed();
+            if constexpr (HD_STAGGER && A == 2 && B == 1) {
+                fft_forward2_staggered<S, E>(v, sm, twS, tau);
+            } else {
+                fft_forward<S, E, A>(v, sm, twS, tau);
+            }
+            if (r == a.r_end - 1) consumed();
             if constexpr (OSM) {
                 T twe[E];
 #pragma unroll
-                for (int e = 0; e < E; ++e) twe[e] = R0 ? mk<T>(1, 0) : ldtw(twr + tau + TT * e);
+                for (int e = 0; e < E; ++e) twe[e] = R0 ? mk<T>(1, 0) : twist_at<TT>(twr, tb, tau, e);
 #pragma unroll 1
                 for (int b = 0; b < B; ++b) {
                     T p[E];
@@ -326,7 +361,7 @@ __device__ __forceinline__ void conv1d_body(const ConvArgs& a, int64_t inst, boo
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const int j = tau + TT * e;
-                const T tw = R0 ? mk<T>(1, 0) : ldtw(twr + j);
+                const T tw = R0 ? mk<T>(1, 0) : twist_at<TT>(twr, tb, tau, e);
 #pragma unroll
                 for (int b = 0; b < B; ++b) {
                     const int o = b * 2 * E + 2 * e;
@@ -341,24 +376,26 @@ __device__ __forceinline__ void conv1d_body(const ConvArgs& a, int64_t inst, boo
                 }
             }
         };
-        residue(0, BoolTag<true>{});
-        for (int r = 1; r < a.n; ++r) residue(r, BoolTag<false>{});
+        if (a.r_begin == 0) residue(0, BoolTag<true>{});
+        for (int r = a.r_begin > 0 ? a.r_begin : 1; r < a.r_end; ++r) residue(r, BoolTag<false>{});
     } else {
         // residue pair (r1, r1 + 1); R0: r1 = 0, whose twists are all 1
         auto pair = [&](int r1, auto r0_tag) {
             constexpr bool R0 = decltype(r0_tag)::value;
             const int r2 = r1 + 1;
-            const bool has2 = r2 < a.n;
+            const bool has2 = r2 < a.r_end;
             const T* twr1 = twN + (int64_t)r1 * S;
             const T* twr2 = twN + (int64_t)(has2 ? r2 : r1) * S;
             const T cr1 = R0 ? mk<T>(1, 0) : cconj(ldtw(twN + (int64_t)a.n * S + r1));      // zeta_N^{-r1 S}
             const T cr2 = has2 ? cconj(ldtw(twN + (int64_t)a.n * S + r2)) : czero<T>();
+            const T tb1 = R0 ? mk<T>(1, 0) : ldtw(twr1 + tau);
+            const T tb2 = has2 ? ldtw(twr2 + tau) : czero<T>();
             T v[A * E];
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const int j = tau + TT * e;
-                const T t1 = R0 ? mk<T>(1, 0) : ldtw(twr1 + j);
-                const T t2 = has2 ? ldtw(twr2 + j) : czero<T>();
+                const T t1 = R0 ? mk<T>(1, 0) : twist_at<TT>(twr1, tb1, tau, e);
+                const T t2 = has2 ? twist_at<TT>(twr2, tb2, tau, e) : czero<T>();
 #pragma unroll
                 for (int aa = 0; aa < A; ++aa) {
                     T b0, b1;
@@ -368,8 +405,12 @@ __device__ __forceinline__ void conv1d_body(const ConvArgs& a, int64_t inst, boo
                     v[aa * E + e] = mk<T>(w1.x - w2.y, w1.y + w2.x);   // W1 + i W2
                 }
             }
-            fft_forward<S, E, A>(v, sm, twS, tau);
-            if (r1 + 2 >= a.n) consumed();
+            if constexpr (HD_STAGGER && A == 2 && B == 1) {
+                fft_forward2_staggered<S, E>(v, sm, twS, tau);
+            } else {
+                fft_forward<S, E, A>(v, sm, twS, tau);
+            }
+            if (r1 + 2 >= a.r_end) consumed();
             if constexpr (OSM) {
 #pragma unroll 1
                 for (int b = 0; b < B; ++b) {
@@ -391,8 +432,8 @@ __device__ __forceinline__ void conv1d_body(const ConvArgs& a, int64_t inst, boo
 #pragma unroll
                     for (int e = 0; e < E; ++e) {
                         const int j = tau + TT * e;
-                        const T t1 = R0 ? mk<T>(1, 0) : ldtw(twr1 + j);
-                        const T t2 = has2 ? ldtw(twr2 + j) : czero<T>();
+                        const T t1 = R0 ? mk<T>(1, 0) : twist_at<TT>(twr1, tb1, tau, e);
+                        const T t2 = has2 ? twist_at<TT>(twr2, tb2, tau, e) : czero<T>();
                         const T ym = sm[padidx((S - j) & (S - 1))];
                         const T yj = p[e];
                         const R hf = R(0.5);
@@ -434,8 +475,8 @@ __device__ __forceinline__ void conv1d_body(const ConvArgs& a, int64_t inst, boo
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const int j = tau + TT * e;
-                const T t1 = R0 ? mk<T>(1, 0) : ldtw(twr1 + j);
-                const T t2 = has2 ? ldtw(twr2 + j) : czero<T>();
+                const T t1 = R0 ? mk<T>(1, 0) : twist_at<TT>(twr1, tb1, tau, e);
+                const T t2 = has2 ? twist_at<TT>(twr2, tb2, tau, e) : czero<T>();
 #pragma unroll
                 for (int b = 0; b < B; ++b) {
                     const int o = b * 2 * E + 2 * e;
@@ -453,8 +494,8 @@ __device__ __forceinline__ void conv1d_body(const ConvArgs& a, int64_t inst, boo
             }
             __syncthreads();
         };
-        pair(0, BoolTag<true>{});
-        for (int r1 = 2; r1 < a.n; r1 += 2) pair(r1, BoolTag<false>{});
+        if (a.r_begin == 0) pair(0, BoolTag<true>{});
+        for (int r1 = a.r_begin > 0 ? a.r_begin : 2; r1 < a.r_end; r1 += 2) pair(r1, BoolTag<false>{});
     }
 
     if (!valid) return;
@@ -633,8 +674,12 @@ __global__ void __launch_bounds__(ConvLaunch<S, E>::MAXT, MINB) conv1d_kernel_pi
         __syncthreads();
         if (!s_ok) {
             if (threadIdx.x == 0) {
-                if (a.err) atomicExch(a.err, 1);
-                if (NBUF == 2 && kn < nsteps) mbar_wait(&bar[b ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
+                // the copies this CTA issued may still be in flight: wait for each once
+                // more (bounded) before the CTA leaves; 2 records that one had not landed
+                int code = 1;
+                if (!mbar_wait(&bar[b], parity)) code = 2;
+                if (NBUF == 2 && kn < nsteps && !mbar_wait(&bar[b ^ 1], (uint32_t)(((it + 1) >> 1) & 1))) code = 2;
+                if (a.err) atomicMax(a.err, code);
             }
             return;
         }
@@ -707,10 +752,10 @@ __global__ void __launch_bounds__(S / E) conv1d_cluster_kernel(const __grid_cons
         if constexpr (NB == 2) s1[e] = R(0);
     }
     R dummy = R(0);
-    const int nsteps = (a.n + D - 1) / D;
+    const int nsteps = (a.r_end - a.r_begin + D - 1) / D;
     for (int k = 0; k < nsteps; ++k) {
-        const int r = g + k * D;
-        const bool act = r < a.n;             // uniform over the CTA
+        const int r = a.r_begin + g + k * D;
+        const bool act = r < a.r_end;         // uniform over the CTA
         T* spk = spec + (k & 1) * S;
         T cr = ldtw(twN + (int64_t)a.n * S + (act ? r : 0));   // zeta_N^{r S}
         if constexpr (KIND == KIND_CENTERED) cr = cconj(cr);

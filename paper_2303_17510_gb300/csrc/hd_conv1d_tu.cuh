@@ -57,7 +57,11 @@ cudaError_t launch_pipe(const ConvArgs& a0, cudaStream_t st, bool* used) {
     constexpr int T = S / E;
     constexpr int A = MultShape<MULT>::A;
     constexpr int NX = MultShape<MULT>::NX;
+#ifdef HD_NBUF_ONE
+    constexpr int NBUF = 1;
+#else
     constexpr int NBUF = MINB == 1 ? 2 : 1;
+#endif
     *used = false;
     static const bool enabled = [] {
         const char* e = std::getenv("HD_PIPE");

@@ -251,6 +251,20 @@ __device__ __forceinline__ T ldtw(const T* p) {
 // tw_offset), read through the read-only data cache.
 template <class T>
 struct TwGlobal {
+    static constexpr bool kProducts = false;
+    const T* __restrict__ p;
+    __device__ __forceinline__ T operator()(int idx) const { return __ldg(p + idx); }
+};
+
+// The same table, of which a radix-8 or -16 pass reads only the powers
+// zeta^{c k1} with k1 = 1, 2, 4 (and 8) and forms the others as products of
+// two of them (each product within two roundings of the table value).  The
+// loads and the FP32 work then both pass through the pipes that bound the
+// fused kernels: this trades 4 (radix 8) or 11 (radix 16) table reads per
+// pass for as many complex multiplies.
+template <class T>
+struct TwGlobalProducts {
+    static constexpr bool kProducts = true;
     const T* __restrict__ p;
     __device__ __forceinline__ T operator()(int idx) const { return __ldg(p + idx); }
 };
@@ -258,9 +272,58 @@ struct TwGlobal {
 // Twiddle source for the FFT passes: the same table copied into shared memory.
 template <class T>
 struct TwShared {
+    static constexpr bool kProducts = false;
     const T* p;
     __device__ __forceinline__ T operator()(int idx) const { return p[idx]; }
 };
+
+// w[k1] = row[k1 Q] for k1 = 1 .. R-1 of a table whose rows k1 hold the powers
+// zeta^{c k1} (row points at column c of row 0, Q entries per row, Q known at
+// run time): every entry read (PRODUCTS = false), or for R >= 8 only the rows
+// 1, 2, 4 (and 8) and the others as products of two of them.
+template <int R, bool PRODUCTS, class T>
+__device__ __forceinline__ void power_row_twiddles(const T* row, int64_t Q, T* w) {
+    if constexpr (PRODUCTS && R >= 8) {
+        w[1] = ldtw(row + Q);
+        w[2] = ldtw(row + 2 * Q);
+        w[4] = ldtw(row + 4 * Q);
+        w[3] = cmul(w[2], w[1]);
+        w[5] = cmul(w[4], w[1]);
+        w[6] = cmul(w[4], w[2]);
+        w[7] = cmul(w[4], w[3]);
+        if constexpr (R == 16) {
+            w[8] = ldtw(row + 8 * Q);
+#pragma unroll
+            for (int k1 = 9; k1 < 16; ++k1) w[k1] = cmul(w[8], w[k1 - 8]);
+        }
+    } else {
+#pragma unroll
+        for (int k1 = 1; k1 < R; ++k1) w[k1] = ldtw(row + k1 * Q);
+    }
+}
+
+// w[k1] = zeta_{N_k}^{c k1}, k1 = 1 .. R-1, for column c of a pass whose table
+// starts at OFF with Q columns per k1.
+template <int R, int Q, int OFF, class T, class TW>
+__device__ __forceinline__ void pass_twiddles(const TW& tw, int c, T* w) {
+    if constexpr (TW::kProducts && R >= 8) {
+        w[1] = tw(OFF + c);
+        w[2] = tw(OFF + Q + c);
+        w[4] = tw(OFF + 3 * Q + c);
+        w[3] = cmul(w[2], w[1]);
+        w[5] = cmul(w[4], w[1]);
+        w[6] = cmul(w[4], w[2]);
+        w[7] = cmul(w[4], w[3]);
+        if constexpr (R == 16) {
+            w[8] = tw(OFF + 7 * Q + c);
+#pragma unroll
+            for (int k1 = 9; k1 < 16; ++k1) w[k1] = cmul(w[8], w[k1 - 8]);
+        }
+    } else {
+#pragma unroll
+        for (int k1 = 1; k1 < R; ++k1) w[k1] = tw(OFF + (k1 - 1) * Q + c);
+    }
+}
 
 // Pass k on NA independent arrays held back to back in v (array a in
 // v[a*E .. a*E+E)): radix-R DFT, then the twiddle zeta_{N_k}^{c k1} (forward);
@@ -283,13 +346,14 @@ __device__ __forceinline__ void fft_pass(T* v, const TW& tw, int tau) {
             for (int a = 0; a < NA; ++a) dft_reg<R, false>(v + a * E + beta * R);
         }
         if constexpr (Q > 1) {
+            T w[R];
+            pass_twiddles<R, Q, OFF>(tw, c, w);            // zeta_{N_k}^{c k1}
 #pragma unroll
             for (int k1 = 1; k1 < R; ++k1) {
-                const T w = tw(OFF + (k1 - 1) * Q + c);   // zeta_{N_k}^{c k1}
 #pragma unroll
                 for (int a = 0; a < NA; ++a) {
                     T& x = v[a * E + beta * R + k1];
-                    x = INV ? cmulc(x, w) : cmul(x, w);
+                    x = INV ? cmulc(x, w[k1]) : cmul(x, w[k1]);
                 }
             }
         }
@@ -307,76 +371,90 @@ __device__ __forceinline__ void fft_pass(T* v, const TW& tw, int tau) {
 // before the buffers are written again.  CST > 1 interleaves the buffers of
 // CST independent transforms (one per column of a column tile): slot s of the
 // transform held by this thread is at sm[s * CST], sm pointing at its column.
-template <int S, int E, int k, bool FWD, int NA, int CST, class T>
-__device__ __forceinline__ void fft_exchange(T* v, T* sm, int tau) {
+// Addressing of exchange k (between pass k and pass k+1): the slot pass k
+// writes for (beta, k1) and the slot pass k+1 reads for (beta, i).  Pad
+// elements per 16: 1, or 2 for the radix-8 reads with 1 < Qn < 16, whose
+// half-warps otherwise meet two words in one bank (checked on the CPU for
+// every exchange of E = 8 and 16, tests/test_fft_exchange_cpu.py: the writes
+// and reads of each exchange are then conflict-free, and every index stays
+// below SMEM).  Column tiles (CST > 1) keep 1.
+template <int S, int E, int k, int CST>
+struct Exch {
     using Sh = FftShape<S, E>;
-    constexpr int R = Sh::radix(k);
-    constexpr int V = S / R;
-    constexpr int Rn = Sh::radix(k + 1);
-    constexpr int Qn = Sh::sub(k + 1) / Rn;
-    // Pad elements per 16: 1, or 2 for the radix-8 reads with 1 < Qn < 16, whose
-    // half-warps otherwise meet two words in one bank (checked on the CPU for
-    // every exchange of E = 8 and 16, tests/test_fft_exchange_cpu.py: the
-    // writes and reads of each exchange are then conflict-free, and every
-    // index stays below SMEM).  Column tiles (CST > 1) keep 1.
-    constexpr int PADM = (CST == 1 && Rn == 8 && Qn > 1 && Qn < 16) ? 2 : 1;
+    static constexpr int R = Sh::radix(k);
+    static constexpr int V = S / R;
+    static constexpr int Rn = Sh::radix(k + 1);
+    static constexpr int Qn = Sh::sub(k + 1) / Rn;
+    static constexpr int PADM = (CST == 1 && Rn == 8 && Qn > 1 && Qn < 16) ? 2 : 1;
     static_assert(PADM == 1 || E == 8, "two pad elements per 16 only fit the E = 8 buffers");
-    auto padk = [](int a) { return a + (a >> 4) * PADM; };
-    if constexpr (FWD) {
+    __device__ __forceinline__ static int padk(int a) { return a + (a >> 4) * PADM; }
+    // slot of value k1 of virtual thread nu after pass k
+    __device__ __forceinline__ static int out_slot(int pn, int nu, int k1) {
+        return (V % 16 == 0) ? pn + V * k1 + (V / 16) * PADM * k1 : padk(nu + V * k1);
+    }
+    // slot of value i of virtual thread nu before pass k + 1
+    __device__ __forceinline__ static int in_slot(int pb, int base, int i) {
+        return (Qn % 16 == 0) ? pb + i * Qn + (Qn / 16) * PADM * i : padk(base + i * Qn);
+    }
+};
+
+// One half of exchange k for NA arrays (array a in the padded buffer
+// sm + a * SMEM): AFTER = true moves the layout after pass k (the forward
+// direction writes it, the inverse reads it), AFTER = false the layout pass
+// k + 1 reads.  STORE: registers to shared memory, else the reverse.
+template <int S, int E, int k, bool AFTER, bool STORE, int NA, int CST, class T>
+__device__ __forceinline__ void exch_half(T* v, T* sm, int tau) {
+    using Sh = FftShape<S, E>;
+    using X = Exch<S, E, k, CST>;
+    if constexpr (AFTER) {
 #pragma unroll
-        for (int beta = 0; beta < E / R; ++beta) {
+        for (int beta = 0; beta < E / X::R; ++beta) {
             const int nu = tau + Sh::T * beta;
-            const int pn = padk(nu);
+            const int pn = X::padk(nu);
 #pragma unroll
-            for (int k1 = 0; k1 < R; ++k1) {
-                const int idx = (V % 16 == 0) ? pn + V * k1 + (V / 16) * PADM * k1 : padk(nu + V * k1);
+            for (int k1 = 0; k1 < X::R; ++k1) {
+                const int idx = X::out_slot(pn, nu, k1);
 #pragma unroll
-                for (int a = 0; a < NA; ++a) sm[(a * Sh::SMEM + idx) * CST] = v[a * E + beta * R + k1];
+                for (int a = 0; a < NA; ++a) {
+                    T& r = v[a * E + beta * X::R + k1];
+                    T& m = sm[(a * Sh::SMEM + idx) * CST];
+                    if constexpr (STORE) m = r; else r = m;
+                }
             }
         }
-        __syncthreads();
-#pragma unroll
-        for (int beta = 0; beta < E / Rn; ++beta) {
-            const int nu = tau + Sh::T * beta;
-            const int b = nu / Qn, c = nu & (Qn - 1);
-            const int base = b * Rn * Qn + c;
-            const int pb = padk(base);
-#pragma unroll
-            for (int i = 0; i < Rn; ++i) {
-                const int idx = (Qn % 16 == 0) ? pb + i * Qn + (Qn / 16) * PADM * i : padk(base + i * Qn);
-#pragma unroll
-                for (int a = 0; a < NA; ++a) v[a * E + beta * Rn + i] = sm[(a * Sh::SMEM + idx) * CST];
-            }
-        }
-        __syncthreads();
     } else {
 #pragma unroll
-        for (int beta = 0; beta < E / Rn; ++beta) {
+        for (int beta = 0; beta < E / X::Rn; ++beta) {
             const int nu = tau + Sh::T * beta;
-            const int b = nu / Qn, c = nu & (Qn - 1);
-            const int base = b * Rn * Qn + c;
-            const int pb = padk(base);
+            const int b = nu / X::Qn, c = nu & (X::Qn - 1);
+            const int base = b * X::Rn * X::Qn + c;
+            const int pb = X::padk(base);
 #pragma unroll
-            for (int i = 0; i < Rn; ++i) {
-                const int idx = (Qn % 16 == 0) ? pb + i * Qn + (Qn / 16) * PADM * i : padk(base + i * Qn);
+            for (int i = 0; i < X::Rn; ++i) {
+                const int idx = X::in_slot(pb, base, i);
 #pragma unroll
-                for (int a = 0; a < NA; ++a) sm[(a * Sh::SMEM + idx) * CST] = v[a * E + beta * Rn + i];
+                for (int a = 0; a < NA; ++a) {
+                    T& r = v[a * E + beta * X::Rn + i];
+                    T& m = sm[(a * Sh::SMEM + idx) * CST];
+                    if constexpr (STORE) m = r; else r = m;
+                }
             }
         }
-        __syncthreads();
-#pragma unroll
-        for (int beta = 0; beta < E / R; ++beta) {
-            const int nu = tau + Sh::T * beta;
-            const int pn = padk(nu);
-#pragma unroll
-            for (int k1 = 0; k1 < R; ++k1) {
-                const int idx = (V % 16 == 0) ? pn + V * k1 + (V / 16) * PADM * k1 : padk(nu + V * k1);
-#pragma unroll
-                for (int a = 0; a < NA; ++a) v[a * E + beta * R + k1] = sm[(a * Sh::SMEM + idx) * CST];
-            }
-        }
-        __syncthreads();
     }
+}
+
+// Exchange between pass k and pass k+1 for NA arrays (array a uses the padded
+// buffer sm + a * SMEM).  FWD: from the layout after pass k to the layout pass
+// k+1 reads; otherwise the reverse.  Two barriers: after the writes, and
+// before the buffers are written again.  CST > 1 interleaves the buffers of
+// CST independent transforms (one per column of a column tile): slot s of the
+// transform held by this thread is at sm[s * CST], sm pointing at its column.
+template <int S, int E, int k, bool FWD, int NA, int CST, class T>
+__device__ __forceinline__ void fft_exchange(T* v, T* sm, int tau) {
+    exch_half<S, E, k, FWD, true, NA, CST>(v, sm, tau);
+    __syncthreads();
+    exch_half<S, E, k, !FWD, false, NA, CST>(v, sm, tau);
+    __syncthreads();
 }
 
 template <int S, int E, int k, int NA, int CST, class T, class TW>
@@ -408,6 +486,52 @@ __device__ __forceinline__ void fft_forward(T* v, T* sm, const TW& tw, int tau) 
 template <int S, int E, int NA = 1, int CST = 1, class T, class TW>
 __device__ __forceinline__ void fft_inverse(T* v, T* sm, const TW& tw, int tau) {
     fft_inv_from<S, E, FftShape<S, E>::K - 1, NA, CST>(v, sm, tw, tau);
+}
+
+// Step k of fft_forward2_staggered: array a has finished pass k, array b pass
+// k - 1 (k > 0) or nothing (k = 0).
+template <int S, int E, int k, class T, class TW>
+__device__ __forceinline__ void stagger_step(T* va, T* vb, T* sa, T* sb, const TW& tw, int tau) {
+    using Sh = FftShape<S, E>;
+    if constexpr (k + 1 < Sh::K) {
+        exch_half<S, E, k, true, true, 1, 1>(va, sa, tau);          // a: write exchange k
+        if constexpr (k > 0) exch_half<S, E, k - 1, false, false, 1, 1>(vb, sb, tau);   // b: read exchange k-1
+        fft_pass<S, E, k, false, 1>(vb, tw, tau);                   // b: pass k
+        __syncthreads();
+        exch_half<S, E, k, false, false, 1, 1>(va, sa, tau);        // a: read exchange k
+        exch_half<S, E, k, true, true, 1, 1>(vb, sb, tau);          // b: write exchange k
+        fft_pass<S, E, k + 1, false, 1>(va, tw, tau);               // a: pass k+1
+        __syncthreads();
+        stagger_step<S, E, k + 1>(va, vb, sa, sb, tw, tau);
+    } else {
+        // a is done; b has written exchange k-1
+        exch_half<S, E, k - 1, false, false, 1, 1>(vb, sb, tau);
+        fft_pass<S, E, k, false, 1>(vb, tw, tau);
+    }
+}
+
+// Forward FFT of two arrays (v[0..E) in buffer sm, v[E..2E) in sm + SMEM),
+// the second one pass behind the first: between two barriers one array's
+// shared-memory traffic meets the other's butterflies, so every phase mixes
+// the two kinds of work (the same arithmetic as fft_forward<S, E, 2>, one
+// barrier per pass instead of two per exchange).  Barrier order: a buffer is
+// written only after a barrier that follows the last read of its previous
+// contents, and read only after a barrier that follows the write.  On return
+// the second buffer may still be read by other threads: the caller's next
+// write to it must follow a barrier (fft_inverse on the first buffer has one).
+template <int S, int E, class T, class TW>
+__device__ __forceinline__ void fft_forward2_staggered(T* v, T* sm, const TW& tw, int tau) {
+    using Sh = FftShape<S, E>;
+    T* va = v;
+    T* vb = v + E;
+    T* sa = sm;
+    T* sb = sm + Sh::SMEM;
+    fft_pass<S, E, 0, false, 1>(va, tw, tau);
+    if constexpr (Sh::K == 1) {
+        fft_pass<S, E, 0, false, 1>(vb, tw, tau);
+    } else {
+        stagger_step<S, E, 0>(va, vb, sa, sb, tw, tau);
+    }
 }
 
 // Frequency index held by register e of thread tau in the spectral layout.

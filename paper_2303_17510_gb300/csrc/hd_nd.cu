@@ -106,20 +106,22 @@ int64_t ncols_of(const hd_plan& pl, int level) {
 }
 
 hd_status exec_level(const hd_plan& pl, int level, int64_t cnt, const void* const* f, int64_t inst_stride,
-                     void* const* h, cudaStream_t st);
+                     void* const* h, int64_t r_begin, int64_t r_end, cudaStream_t st);
 
 // One pass of outer level `level` over `cnt` instances (at most the level's
 // chunk): residue transforms along the axis, the sub-convolutions of the
-// transformed slices, inverse transforms.
+// transformed slices, inverse transforms.  Residues r_begin <= r < r_end of
+// the axis only (the partial sums of a residue-sharded convolution, on the
+// outermost axis; every residue on the inner ones).
 hd_status exec_level_pass(const hd_plan& pl, int level, int64_t cnt, const void* const* f, int64_t inst_stride,
-                          void* const* h, cudaStream_t st) {
+                          void* const* h, int64_t r_begin, int64_t r_end, cudaStream_t st) {
     const AxisPlan& ax = pl.ax[level];
     const int64_t ncols = ncols_of(pl, level);
     const size_t esz = pl.dtype == HD_F64 ? 16 : 8;
     const int nr = ax.D > 0 && ax.D < ax.n ? ax.D : (int)ax.n;
     const int outer_kind = ax.kind == HD_COMPLEX ? KIND_COMPLEX : KIND_CENTERED;
-    for (int r0 = 0; r0 < ax.n; r0 += nr) {
-        const int nrb = (int)(ax.n - r0 < nr ? ax.n - r0 : nr);
+    for (int r0 = (int)r_begin; r0 < r_end; r0 += nr) {
+        const int nrb = (int)(r_end - r0 < nr ? r_end - r0 : nr);
         ColArgs a = make_col_args(pl, ax, level, cnt, inst_stride, ncols, r0, nrb);
         for (int i = 0; i < pl.A; ++i) a.f[i] = f[i];
         cudaError_t e = pl.dtype == HD_F64 ? col_launch_f64(a, outer_kind, false, true, st)
@@ -132,10 +134,10 @@ hd_status exec_level_pass(const hd_plan& pl, int level, int64_t cnt, const void*
         void* gh[kMaxOut];
         for (int i = 0; i < pl.A; ++i) g[i] = static_cast<const char*>(pl.work[level]) + (size_t)i * sub * ncols * esz;
         for (int b = 0; b < pl.B; ++b) gh[b] = static_cast<char*>(pl.work[level]) + (size_t)b * sub * ncols * esz;
-        hd_status s2 = exec_level(pl, level + 1, sub, g, ncols, gh, st);
+        hd_status s2 = exec_level(pl, level + 1, sub, g, ncols, gh, 0, pl.ax[level + 1].n, st);
         if (s2 != HD_OK) return s2;
         for (int b = 0; b < pl.B; ++b) a.h[b] = h[b];
-        a.accumulate = r0 > 0;
+        a.accumulate = r0 > r_begin;
         e = pl.dtype == HD_F64 ? col_launch_f64(a, outer_kind, false, false, st)
                                : col_launch_f32(a, outer_kind, false, false, st);
         if (e != cudaSuccess) return HD_ERR_CUDA;
@@ -149,7 +151,7 @@ hd_status exec_level_pass(const hd_plan& pl, int level, int64_t cnt, const void*
 // (the level's chunk), each chunk's forward transforms, sub-convolutions and
 // inverse transforms while its work buffer is L2-resident.
 hd_status exec_level(const hd_plan& pl, int level, int64_t cnt, const void* const* f, int64_t inst_stride,
-                     void* const* h, cudaStream_t st) {
+                     void* const* h, int64_t r_begin, int64_t r_end, cudaStream_t st) {
     const AxisPlan& ax = pl.ax[level];
     if (level == pl.ndim - 1) return rows_execute(pl, ax, cnt, f, h, inst_stride, pl.scratch, st);
     const size_t esz = pl.dtype == HD_F64 ? 16 : 8;
@@ -160,7 +162,7 @@ hd_status exec_level(const hd_plan& pl, int level, int64_t cnt, const void* cons
         void* hc[kMaxOut];
         for (int a = 0; a < pl.A; ++a) fc[a] = static_cast<const char*>(f[a]) + (size_t)(c0 * inst_stride) * esz;
         for (int b = 0; b < pl.B; ++b) hc[b] = static_cast<char*>(h[b]) + (size_t)(c0 * inst_stride) * esz;
-        hd_status s2 = exec_level_pass(pl, level, cc, fc, inst_stride, hc, st);
+        hd_status s2 = exec_level_pass(pl, level, cc, fc, inst_stride, hc, r_begin, r_end, st);
         if (s2 != HD_OK) return s2;
     }
     return HD_OK;
@@ -306,14 +308,14 @@ hd_status plan_create_nd(hd_plan** out, const hd_desc* d) {
 }
 
 hd_status plan_execute_nd(hd_plan* pl, int64_t count, const void* const* f, void* const* h, int64_t stride,
-                          cudaStream_t st) {
+                          int64_t r_begin, int64_t r_end, cudaStream_t st) {
     const size_t esz = pl->dtype == HD_F64 ? 16 : 8;
     for (int64_t i = 0; i < count; ++i) {
         const void* fi[3];
         void* hi[kMaxOut];
         for (int a = 0; a < pl->A; ++a) fi[a] = static_cast<const char*>(f[a]) + (size_t)(i * stride) * esz;
         for (int b = 0; b < pl->B; ++b) hi[b] = static_cast<char*>(h[b]) + (size_t)(i * stride) * esz;
-        hd_status s2 = exec_level(*pl, 0, 1, fi, pl->instance_elems, hi, st);
+        hd_status s2 = exec_level(*pl, 0, 1, fi, pl->instance_elems, hi, r_begin, r_end, st);
         if (s2 != HD_OK) return s2;
     }
     return HD_OK;

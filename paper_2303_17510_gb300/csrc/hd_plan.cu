@@ -292,6 +292,8 @@ ConvArgs make_conv_args(const hd_plan& pl, const AxisPlan& ax, int64_t count, co
     a.twS = ax.twS;
     a.twN = ax.twN;
     a.invN = 1.0 / (double)(ax.n * ax.S);
+    a.r_begin = 0;
+    a.r_end = (int)ax.n;
     return a;
 }
 
@@ -338,20 +340,26 @@ SplitArgs make_split_args(const hd_plan& pl, const AxisPlan& ax, int64_t first, 
 
 hd_status split_execute(const hd_plan& pl, const AxisPlan& ax, int64_t count, const void* const* f, void* const* h,
                         int64_t stride, void* work, int64_t chunk, cudaStream_t st) {
+    return split_execute_range(pl, ax, count, f, h, stride, work, chunk, 0, ax.n, st);
+}
+
+hd_status split_execute_range(const hd_plan& pl, const AxisPlan& ax, int64_t count, const void* const* f,
+                              void* const* h, int64_t stride, void* work, int64_t chunk, int64_t r_begin,
+                              int64_t r_end, cudaStream_t st) {
     const int mult = kernel_mult(pl.mult);
     const int64_t blk = split_block(ax);
     // residue blocks re-read the inputs after the first block has written the
     // output, so blocked plans cannot write over their inputs
-    if (blk < ax.n)
+    if (r_begin + blk < r_end)
         for (int a = 0; a < pl.A; ++a)
             if (f[a] == h[0]) return HD_ERR_INVALID;
     for (int64_t first = 0; first < count; first += chunk) {
         const int64_t cnt = count - first < chunk ? count - first : chunk;
         SplitArgs a = make_split_args(pl, ax, first, cnt, f, h, stride, work);
-        for (int64_t r0 = 0; r0 < ax.n; r0 += blk) {
+        for (int64_t r0 = r_begin; r0 < r_end; r0 += blk) {
             a.r0 = (int)r0;
-            a.nr = (int)(ax.n - r0 < blk ? ax.n - r0 : blk);
-            a.accumulate = r0 > 0;
+            a.nr = (int)(r_end - r0 < blk ? r_end - r0 : blk);
+            a.accumulate = r0 > r_begin;
             cudaError_t e = pl.dtype == HD_F64 ? split_launch_f64(a, ax.kind, mult, ax.comp, st)
                                                : split_launch_f32(a, ax.kind, mult, ax.comp, st);
             if (e != cudaSuccess) return HD_ERR_CUDA;
@@ -369,20 +377,27 @@ hd_status rows_execute(const hd_plan& pl, const AxisPlan& ax, int64_t count, con
 
 hd_status plan_execute(hd_plan* pl, int64_t count, const void* const* f, void* const* h, int64_t stride,
                        cudaStream_t st) {
+    return plan_execute_range(pl, count, f, h, stride, 0, pl->ax[0].n, st);
+}
+
+hd_status plan_execute_range(hd_plan* pl, int64_t count, const void* const* f, void* const* h, int64_t stride,
+                             int64_t r_begin, int64_t r_end, cudaStream_t st) {
     DeviceGuard g(pl->device);
     if (pl->ndim > 1) {
-        hd_status s2 = plan_execute_nd(pl, count, f, h, stride, st);
+        hd_status s2 = plan_execute_nd(pl, count, f, h, stride, r_begin, r_end, st);
         if (s2 != HD_OK) pl->sticky = s2;
         return s2;
     }
     const AxisPlan& ax = pl->ax[0];
     if (ax.path == PATH_SPLIT) {
         if (!pl->scratch) return HD_ERR_UNSUPPORTED;   // created without a work buffer
-        hd_status s2 = split_execute(*pl, ax, count, f, h, stride, pl->scratch, ax.chunk, st);
+        hd_status s2 = split_execute_range(*pl, ax, count, f, h, stride, pl->scratch, ax.chunk, r_begin, r_end, st);
         if (s2 == HD_ERR_CUDA) pl->sticky = s2;
         return s2;
     }
     ConvArgs a = make_conv_args(*pl, ax, count, f, h, stride);
+    a.r_begin = (int)r_begin;
+    a.r_end = (int)r_end;
     const bool cluster = ax.D > 1 && ax.kind != HD_HERMITIAN;
     cudaError_t e = cluster ? conv1d_cluster_launch(fused_cfg(*pl, ax), a, ax.D, st)
                             : conv1d_launch(fused_cfg(*pl, ax), a, st);

@@ -118,6 +118,10 @@ namespace hd {
 hd_status plan_create(hd_plan** out, const hd_desc* d);
 hd_status plan_execute(hd_plan* plan, int64_t count, const void* const* f, void* const* h, int64_t stride,
                        cudaStream_t st);
+// the partial sum over residues r_begin <= r < r_end of the outermost axis
+// (0 <= r_begin < r_end <= n; 0, n is plan_execute)
+hd_status plan_execute_range(hd_plan* plan, int64_t count, const void* const* f, void* const* h, int64_t stride,
+                             int64_t r_begin, int64_t r_end, cudaStream_t st);
 void plan_free(hd_plan* plan);
 ConvArgs make_conv_args(const hd_plan& pl, const AxisPlan& ax, int64_t count, const void* const* f,
                         void* const* h, int64_t stride);
@@ -141,7 +145,7 @@ void ragged_destroy(hd_plan* pl);
 // multidimensional plans (hd_nd.cu)
 hd_status plan_create_nd(hd_plan** out, const hd_desc* d);
 hd_status plan_execute_nd(hd_plan* pl, int64_t count, const void* const* f, void* const* h, int64_t stride,
-                          cudaStream_t st);
+                          int64_t r_begin, int64_t r_end, cudaStream_t st);
 // batched 1D convolution of rows with axis plan ax (fused or split path):
 // the A inputs f, the B outputs h
 hd_status rows_execute(const hd_plan& pl, const AxisPlan& ax, int64_t count, const void* const* f,
@@ -158,6 +162,10 @@ bool cache_lookup(const hd_desc* d, hd_candidate* c);
 // Split path over a caller-provided work buffer holding `chunk` instances.
 hd_status split_execute(const hd_plan& pl, const AxisPlan& ax, int64_t count, const void* const* f, void* const* h,
                         int64_t stride, void* work, int64_t chunk, cudaStream_t st);
+// the same for residues r_begin <= r < r_end only
+hd_status split_execute_range(const hd_plan& pl, const AxisPlan& ax, int64_t count, const void* const* f,
+                              void* const* h, int64_t stride, void* work, int64_t chunk, int64_t r_begin,
+                              int64_t r_end, cudaStream_t st);
 
 // Legal, supported (m, p, q) of one axis chosen by the cost model; fills ax.
 hd_status choose_axis(int dtype, int kind, int mult, int A, int B, int64_t L, int64_t M, AxisPlan* ax);

@@ -152,6 +152,9 @@ __device__ __forceinline__ ConvArgs conv_args_of(const RInst& r) {
     a.twS = r.twS;
     a.twN = r.twN;
     a.invN = r.invN;
+    a.err = nullptr;
+    a.r_begin = 0;
+    a.r_end = r.n;
     return a;
 }
 

@@ -63,6 +63,20 @@ __device__ __forceinline__ void l2_discard(const void* p, int64_t bytes, int tid
         asm volatile("discard.global.L2 [%0], 128;" ::"l"(c + off) : "memory");
 }
 
+// Twist zeta_N^{r j}, j = j1 S2 + j2, of residue row twr (= twR + r S): the
+// table entry, or (HD_TWF) tb = zeta_N^{r j2} (one read per column) times the
+// row's entry j1 S2 (the same for every column: a broadcast read).
+template <class T>
+__device__ __forceinline__ T split_twist(const T* twr, T tb, int j1, int j2, int S2) {
+#if HD_TWF
+    (void)j2;
+    return j1 == 0 ? tb : cmul(tb, ldtw(twr + (int64_t)j1 * S2));
+#else
+    (void)tb;
+    return ldtw(twr + (int64_t)j1 * S2 + j2);
+#endif
+}
+
 // Forward column j2 of residue r of input aa of instance inst.
 template <class R, int S1, int KIND>
 __device__ __forceinline__ void split_colfwd_body(const SplitArgs& a, int64_t inst, int aa, int r, int j2) {
@@ -76,19 +90,23 @@ __device__ __forceinline__ void split_colfwd_body(const SplitArgs& a, int64_t in
     ca.H = a.H;
     T cr = ldtw(twR + (int64_t)a.n * a.S + r);      // zeta_N^{r S}
     if constexpr (KIND != KIND_COMPLEX) cr = cconj(cr);
+    const T* twr = twR + (int64_t)r * a.S;
+    const T tb = ldtw(twr + j2);                      // zeta_N^{r j2}
     T v[S1];
 #pragma unroll
     for (int j1 = 0; j1 < S1; ++j1) {
         const int j = j1 * a.S2 + j2;
         T b0, b1;
         load_fold<KIND, true>(f, j, a.S, ca, true, b0, b1);
-        v[j1] = cmul(cadd(b0, cmul(cr, b1)), ldtw(twR + (int64_t)r * a.S + j));
+        v[j1] = cmul(cadd(b0, cmul(cr, b1)), split_twist(twr, tb, j1, j2, a.S2));
     }
     dft_small<S1, false>(v);
+    T tw[S1];
+    power_row_twiddles<S1, HD_TWP != 0>(twS + j2, a.S2, tw);   // zeta_S^{j2 k1}
     T* w = static_cast<T*>(a.work) + ((inst * a.A + aa) * a.nr + (r - a.r0)) * (int64_t)a.S;
 #pragma unroll
     for (int k1 = 0; k1 < S1; ++k1) {
-        const T t = k1 == 0 ? v[0] : cmul(v[k1], ldtw(twS + k1 * a.S2 + j2));
+        const T t = k1 == 0 ? v[0] : cmul(v[k1], tw[k1]);
         w[(int64_t)k1 * a.S2 + j2] = t;
     }
 }
@@ -110,15 +128,18 @@ __device__ __forceinline__ void split_colfwd_multi(const SplitArgs& a, int64_t i
     ca.H = a.H;
     T cr = ldtw(twR + (int64_t)a.n * a.S + r);      // zeta_N^{r S}
     if constexpr (KIND != KIND_COMPLEX) cr = cconj(cr);
+    const T* twr = twR + (int64_t)r * a.S;
     T v[U][S1];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
+        const int j2 = j2base + u * jstep;
+        const T tb = ldtw(twr + j2);                  // zeta_N^{r j2}
 #pragma unroll
         for (int j1 = 0; j1 < S1; ++j1) {
-            const int j = j1 * a.S2 + j2base + u * jstep;
+            const int j = j1 * a.S2 + j2;
             T b0, b1;
             load_fold<KIND, true>(f, j, a.S, ca, true, b0, b1);
-            v[u][j1] = cmul(cadd(b0, cmul(cr, b1)), ldtw(twR + (int64_t)r * a.S + j));
+            v[u][j1] = cmul(cadd(b0, cmul(cr, b1)), split_twist(twr, tb, j1, j2, a.S2));
         }
     }
     T* w = static_cast<T*>(a.work) + ((inst * a.A + aa) * a.nr + (r - a.r0)) * (int64_t)a.S;
@@ -126,9 +147,11 @@ __device__ __forceinline__ void split_colfwd_multi(const SplitArgs& a, int64_t i
     for (int u = 0; u < U; ++u) {
         const int j2 = j2base + u * jstep;
         dft_small<S1, false>(v[u]);
+        T tw[S1];
+        power_row_twiddles<S1, HD_TWP != 0>(twS + j2, a.S2, tw);   // zeta_S^{j2 k1}
 #pragma unroll
         for (int k1 = 0; k1 < S1; ++k1) {
-            const T t = k1 == 0 ? v[u][0] : cmul(v[u][k1], ldtw(twS + k1 * a.S2 + j2));
+            const T t = k1 == 0 ? v[u][0] : cmul(v[u][k1], tw[k1]);
             w[(int64_t)k1 * a.S2 + j2] = t;
         }
     }
@@ -255,17 +278,19 @@ __device__ __forceinline__ void split_colbwd_body(const SplitArgs& a, int64_t in
     for (int r = a.r0; r < a.r0 + a.nr; ++r) {
         T cr = ldtw(twR + (int64_t)a.n * a.S + r);
         if constexpr (KIND != KIND_COMPLEX) cr = cconj(cr);
-        T v[S1];
+        T v[S1], tw[S1];
+        power_row_twiddles<S1, HD_TWP != 0>(twS + j2, a.S2, tw);   // zeta_S^{j2 k1}
 #pragma unroll
         for (int k1 = 0; k1 < S1; ++k1) {
             const T z = base[(int64_t)(r - a.r0) * a.S + (int64_t)k1 * a.S2 + j2];
-            v[k1] = k1 == 0 ? z : cmulc(z, ldtw(twS + k1 * a.S2 + j2));
+            v[k1] = k1 == 0 ? z : cmulc(z, tw[k1]);
         }
         dft_small<S1, true>(v);
+        const T* twr = twR + (int64_t)r * a.S;
+        const T tb = ldtw(twr + j2);                  // zeta_N^{r j2}
 #pragma unroll
         for (int j1 = 0; j1 < S1; ++j1) {
-            const int j = j1 * a.S2 + j2;
-            T y = cmulc(v[j1], ldtw(twR + (int64_t)r * a.S + j));
+            T y = cmulc(v[j1], split_twist(twr, tb, j1, j2, a.S2));
             acc_add<R, COMP>(s0[2 * j1], COMP ? c0[2 * j1] : dummy, y.x);
             acc_add<R, COMP>(s0[2 * j1 + 1], COMP ? c0[2 * j1 + 1] : dummy, y.y);
             if constexpr (NB == 2) {
@@ -333,16 +358,19 @@ __device__ __forceinline__ void split_colbwd_multi(const SplitArgs& a, int64_t i
 #pragma unroll
             for (int k1 = 0; k1 < S1; ++k1)
                 v[u][k1] = base[(int64_t)(r - a.r0) * a.S + (int64_t)k1 * a.S2 + j2base + u * jstep];
+        const T* twr = twR + (int64_t)r * a.S;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int j2 = j2base + u * jstep;
+            T tw[S1];
+            power_row_twiddles<S1, HD_TWP != 0>(twS + j2, a.S2, tw);   // zeta_S^{j2 k1}
 #pragma unroll
-            for (int k1 = 1; k1 < S1; ++k1) v[u][k1] = cmulc(v[u][k1], ldtw(twS + k1 * a.S2 + j2));
+            for (int k1 = 1; k1 < S1; ++k1) v[u][k1] = cmulc(v[u][k1], tw[k1]);
             dft_small<S1, true>(v[u]);
+            const T tb = ldtw(twr + j2);              // zeta_N^{r j2}
 #pragma unroll
             for (int j1 = 0; j1 < S1; ++j1) {
-                const int j = j1 * a.S2 + j2;
-                T y = cmulc(v[u][j1], ldtw(twR + (int64_t)r * a.S + j));
+                T y = cmulc(v[u][j1], split_twist(twr, tb, j1, j2, a.S2));
                 acc_add<R, COMP>(s0[u][2 * j1], COMP ? c0[u][2 * j1] : dummy, y.x);
                 acc_add<R, COMP>(s0[u][2 * j1 + 1], COMP ? c0[u][2 * j1 + 1] : dummy, y.y);
                 if constexpr (NB == 2) {
