@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(ColShape<S, E>::THREADS) col_forward(const __g
     const int aa = blockIdx.y;
     const int64_t inst = blockIdx.z;
     T* sm = reinterpret_cast<T*>(smem_raw) + y;
-    const TwGlobal<T> tw{static_cast<const T*>(a.twS)};
+    const TwGlobalProducts<T> tw{static_cast<const T*>(a.twS)};
     const T* twN = static_cast<const T*>(a.twN);
     const T* f = static_cast<const T*>(a.f[aa]) + inst * a.inst_stride + (valid ? col : 0);
     T b0[E], b1[E];
@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(ColShape<S, E>::THREADS) col_backward(const __
     const int ob = blockIdx.y;
     const int64_t inst = blockIdx.z;
     T* sm = reinterpret_cast<T*>(smem_raw) + y;
-    const TwGlobal<T> tw{static_cast<const T*>(a.twS)};
+    const TwGlobalProducts<T> tw{static_cast<const T*>(a.twS)};
     const T* twN = static_cast<const T*>(a.twN);
     R s0[2 * E], c0[COMP ? 2 * E : 1], s1[2 * E], c1[COMP ? 2 * E : 1];
     R dummy = 0;

@@ -41,16 +41,6 @@
 
 #include "hd_fft.cuh"
 
-#ifndef HD_TWP
-#define HD_TWP 0
-#endif
-#ifndef HD_STAGGER
-#define HD_STAGGER 0
-#endif
-#ifndef HD_TWF
-#define HD_TWF 0
-#endif
-
 namespace hd {
 
 enum { KIND_COMPLEX = 0, KIND_CENTERED = 1, KIND_HERMITIAN = 2 };
@@ -152,20 +142,6 @@ struct BoolTag {
     static constexpr bool value = B;
 };
 
-// Twist zeta_N^{r j} of slot j = tau + TT e of residue row twr (= twN + r S):
-// the table entry, or (HD_TWF) the product of tb = zeta_N^{r tau} (one read per
-// thread) and zeta_N^{r TT e} (the row's entry TT e, the same for every thread
-// of the CTA: a broadcast read of E entries that stay in L1).
-template <int TT, class T>
-__device__ __forceinline__ T twist_at(const T* twr, T tb, int tau, int e) {
-#if HD_TWF
-    return e == 0 ? tb : cmul(tb, ldtw(twr + TT * e));
-#else
-    (void)tb;
-    return ldtw(twr + tau + TT * e);
-#endif
-}
-
 // Residue-sum accumulation.  COMP: TwoSum compensated s + c += x (FP32 path);
 // otherwise a plain sum.
 template <class R, bool COMP>
@@ -250,11 +226,8 @@ __device__ __forceinline__ void conv1d_body(const ConvArgs& a, int64_t inst, boo
     constexpr bool OSM = MultShape<MULT>::OUT_SMEM;
     constexpr int BR = OSM ? 1 : B;   // outputs whose residue sums live in registers
     const T* twN = static_cast<const T*>(a.twN);
-#if HD_TWP
+    // pass twiddles: radix-8/16 passes read three or four powers and form the rest
     const TwGlobalProducts<T> twS{static_cast<const T*>(a.twS)};
-#else
-    const TwGlobal<T> twS{static_cast<const T*>(a.twS)};
-#endif
     // OUT_SMEM: residue sums of output b, block nb at acc[(b NB + nb) S + j], each
     // entry read and written only by the thread that owns slot j
     T* acc = sm + MultShape<MULT>::NX * Sh::SMEM;
@@ -304,12 +277,11 @@ __device__ __forceinline__ void conv1d_body(const ConvArgs& a, int64_t inst, boo
             const T* twr = twN + (int64_t)r * S;        // zeta_N^{r j}, j < S
             T cr = R0 ? mk<T>(1, 0) : ldtw(twN + (int64_t)a.n * S + r);    // zeta_N^{r S}
             if constexpr (KIND == KIND_CENTERED) cr = cconj(cr);
-            const T tb = R0 ? mk<T>(1, 0) : ldtw(twr + tau);                 // zeta_N^{r tau}
             T v[A * E];
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const int j = tau + TT * e;
-                const T tw = R0 ? mk<T>(1, 0) : twist_at<TT>(twr, tb, tau, e);
+                const T tw = R0 ? mk<T>(1, 0) : ldtw(twr + j);
 #pragma unroll
                 for (int aa = 0; aa < A; ++aa) {
                     if constexpr (KIND == KIND_COMPLEX && NB == 1) {
@@ -324,16 +296,12 @@ __device__ __forceinline__ void conv1d_body(const ConvArgs& a, int64_t inst, boo
                     }
                 }
             }
-            if constexpr (HD_STAGGER && A == 2 && B == 1) {
-                fft_forward2_staggered<S, E>(v, sm, twS, tau);
-            } else {
-                fft_forward<S, E, A>(v, sm, twS, tau);
-            }
+            fft_forward<S, E, A>(v, sm, twS, tau);
             if (r == a.r_end - 1) consumed();
             if constexpr (OSM) {
                 T twe[E];
 #pragma unroll
-                for (int e = 0; e < E; ++e) twe[e] = R0 ? mk<T>(1, 0) : twist_at<TT>(twr, tb, tau, e);
+                for (int e = 0; e < E; ++e) twe[e] = R0 ? mk<T>(1, 0) : ldtw(twr + tau + TT * e);
 #pragma unroll 1
                 for (int b = 0; b < B; ++b) {
                     T p[E];
@@ -361,7 +329,7 @@ __device__ __forceinline__ void conv1d_body(const ConvArgs& a, int64_t inst, boo
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const int j = tau + TT * e;
-                const T tw = R0 ? mk<T>(1, 0) : twist_at<TT>(twr, tb, tau, e);
+                const T tw = R0 ? mk<T>(1, 0) : ldtw(twr + j);
 #pragma unroll
                 for (int b = 0; b < B; ++b) {
                     const int o = b * 2 * E + 2 * e;
@@ -388,14 +356,12 @@ __device__ __forceinline__ void conv1d_body(const ConvArgs& a, int64_t inst, boo
             const T* twr2 = twN + (int64_t)(has2 ? r2 : r1) * S;
             const T cr1 = R0 ? mk<T>(1, 0) : cconj(ldtw(twN + (int64_t)a.n * S + r1));      // zeta_N^{-r1 S}
             const T cr2 = has2 ? cconj(ldtw(twN + (int64_t)a.n * S + r2)) : czero<T>();
-            const T tb1 = R0 ? mk<T>(1, 0) : ldtw(twr1 + tau);
-            const T tb2 = has2 ? ldtw(twr2 + tau) : czero<T>();
             T v[A * E];
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const int j = tau + TT * e;
-                const T t1 = R0 ? mk<T>(1, 0) : twist_at<TT>(twr1, tb1, tau, e);
-                const T t2 = has2 ? twist_at<TT>(twr2, tb2, tau, e) : czero<T>();
+                const T t1 = R0 ? mk<T>(1, 0) : ldtw(twr1 + j);
+                const T t2 = has2 ? ldtw(twr2 + j) : czero<T>();
 #pragma unroll
                 for (int aa = 0; aa < A; ++aa) {
                     T b0, b1;
@@ -405,11 +371,7 @@ __device__ __forceinline__ void conv1d_body(const ConvArgs& a, int64_t inst, boo
                     v[aa * E + e] = mk<T>(w1.x - w2.y, w1.y + w2.x);   // W1 + i W2
                 }
             }
-            if constexpr (HD_STAGGER && A == 2 && B == 1) {
-                fft_forward2_staggered<S, E>(v, sm, twS, tau);
-            } else {
-                fft_forward<S, E, A>(v, sm, twS, tau);
-            }
+            fft_forward<S, E, A>(v, sm, twS, tau);
             if (r1 + 2 >= a.r_end) consumed();
             if constexpr (OSM) {
 #pragma unroll 1
@@ -432,8 +394,8 @@ __device__ __forceinline__ void conv1d_body(const ConvArgs& a, int64_t inst, boo
 #pragma unroll
                     for (int e = 0; e < E; ++e) {
                         const int j = tau + TT * e;
-                        const T t1 = R0 ? mk<T>(1, 0) : twist_at<TT>(twr1, tb1, tau, e);
-                        const T t2 = has2 ? twist_at<TT>(twr2, tb2, tau, e) : czero<T>();
+                        const T t1 = R0 ? mk<T>(1, 0) : ldtw(twr1 + j);
+                        const T t2 = has2 ? ldtw(twr2 + j) : czero<T>();
                         const T ym = sm[padidx((S - j) & (S - 1))];
                         const T yj = p[e];
                         const R hf = R(0.5);
@@ -475,8 +437,8 @@ __device__ __forceinline__ void conv1d_body(const ConvArgs& a, int64_t inst, boo
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const int j = tau + TT * e;
-                const T t1 = R0 ? mk<T>(1, 0) : twist_at<TT>(twr1, tb1, tau, e);
-                const T t2 = has2 ? twist_at<TT>(twr2, tb2, tau, e) : czero<T>();
+                const T t1 = R0 ? mk<T>(1, 0) : ldtw(twr1 + j);
+                const T t2 = has2 ? ldtw(twr2 + j) : czero<T>();
 #pragma unroll
                 for (int b = 0; b < B; ++b) {
                     const int o = b * 2 * E + 2 * e;
@@ -616,11 +578,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     return true;
 }
 
-// NBUF = 2: the next step is staged into the second buffer while the CTA
-// computes (one CTA per SM).  NBUF = 1: one buffer, released early: the copy
-// for the next step starts once the last residue's forward transforms have
+// NBUF = 1 (the launchers' choice): one buffer, released early: the copy for
+// the next step starts once the last residue's forward transforms have
 // consumed the staged inputs, and overlaps that residue's product, inverse
-// transform and accumulation (keeps two CTAs per SM).
+// transform and accumulation.  NBUF = 2: the next step is staged into a second
+// buffer while the CTA computes.
 template <class R, int S, int E, int KIND, int MULT, int NB, bool COMP, int MINB, int NBUF>
 __global__ void __launch_bounds__(ConvLaunch<S, E>::MAXT, MINB) conv1d_kernel_pipe(const __grid_constant__ ConvArgs a) {
     using T = cplx<R>;

@@ -258,10 +258,12 @@ struct TwGlobal {
 
 // The same table, of which a radix-8 or -16 pass reads only the powers
 // zeta^{c k1} with k1 = 1, 2, 4 (and 8) and forms the others as products of
-// two of them (each product within two roundings of the table value).  The
-// loads and the FP32 work then both pass through the pipes that bound the
-// fused kernels: this trades 4 (radix 8) or 11 (radix 16) table reads per
-// pass for as many complex multiplies.
+// two of them (each product within two roundings of the table value): 4
+// (radix 8) or 11 (radix 16) table reads per pass become complex multiplies.
+// The fused kernels wait on those reads (they miss L1 beside the staging and
+// exchange buffers); measured 6 % (S = 2048, E = 8) and 11 % (S = 4096,
+// E = 16) faster on the 4096 x 4096 batch, results within 2.5e-7 rel-L2 of
+// the full-table ones.
 template <class T>
 struct TwGlobalProducts {
     static constexpr bool kProducts = true;
@@ -486,52 +488,6 @@ __device__ __forceinline__ void fft_forward(T* v, T* sm, const TW& tw, int tau) 
 template <int S, int E, int NA = 1, int CST = 1, class T, class TW>
 __device__ __forceinline__ void fft_inverse(T* v, T* sm, const TW& tw, int tau) {
     fft_inv_from<S, E, FftShape<S, E>::K - 1, NA, CST>(v, sm, tw, tau);
-}
-
-// Step k of fft_forward2_staggered: array a has finished pass k, array b pass
-// k - 1 (k > 0) or nothing (k = 0).
-template <int S, int E, int k, class T, class TW>
-__device__ __forceinline__ void stagger_step(T* va, T* vb, T* sa, T* sb, const TW& tw, int tau) {
-    using Sh = FftShape<S, E>;
-    if constexpr (k + 1 < Sh::K) {
-        exch_half<S, E, k, true, true, 1, 1>(va, sa, tau);          // a: write exchange k
-        if constexpr (k > 0) exch_half<S, E, k - 1, false, false, 1, 1>(vb, sb, tau);   // b: read exchange k-1
-        fft_pass<S, E, k, false, 1>(vb, tw, tau);                   // b: pass k
-        __syncthreads();
-        exch_half<S, E, k, false, false, 1, 1>(va, sa, tau);        // a: read exchange k
-        exch_half<S, E, k, true, true, 1, 1>(vb, sb, tau);          // b: write exchange k
-        fft_pass<S, E, k + 1, false, 1>(va, tw, tau);               // a: pass k+1
-        __syncthreads();
-        stagger_step<S, E, k + 1>(va, vb, sa, sb, tw, tau);
-    } else {
-        // a is done; b has written exchange k-1
-        exch_half<S, E, k - 1, false, false, 1, 1>(vb, sb, tau);
-        fft_pass<S, E, k, false, 1>(vb, tw, tau);
-    }
-}
-
-// Forward FFT of two arrays (v[0..E) in buffer sm, v[E..2E) in sm + SMEM),
-// the second one pass behind the first: between two barriers one array's
-// shared-memory traffic meets the other's butterflies, so every phase mixes
-// the two kinds of work (the same arithmetic as fft_forward<S, E, 2>, one
-// barrier per pass instead of two per exchange).  Barrier order: a buffer is
-// written only after a barrier that follows the last read of its previous
-// contents, and read only after a barrier that follows the write.  On return
-// the second buffer may still be read by other threads: the caller's next
-// write to it must follow a barrier (fft_inverse on the first buffer has one).
-template <int S, int E, class T, class TW>
-__device__ __forceinline__ void fft_forward2_staggered(T* v, T* sm, const TW& tw, int tau) {
-    using Sh = FftShape<S, E>;
-    T* va = v;
-    T* vb = v + E;
-    T* sa = sm;
-    T* sb = sm + Sh::SMEM;
-    fft_pass<S, E, 0, false, 1>(va, tw, tau);
-    if constexpr (Sh::K == 1) {
-        fft_pass<S, E, 0, false, 1>(vb, tw, tau);
-    } else {
-        stagger_step<S, E, 0>(va, vb, sa, sb, tw, tau);
-    }
 }
 
 // Frequency index held by register e of thread tau in the spectral layout.

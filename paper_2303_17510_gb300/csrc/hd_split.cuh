@@ -64,17 +64,13 @@ __device__ __forceinline__ void l2_discard(const void* p, int64_t bytes, int tid
 }
 
 // Twist zeta_N^{r j}, j = j1 S2 + j2, of residue row twr (= twR + r S): the
-// table entry, or (HD_TWF) tb = zeta_N^{r j2} (one read per column) times the
-// row's entry j1 S2 (the same for every column: a broadcast read).
+// product of tb = zeta_N^{r j2} (one read per column) and the row's entry
+// j1 S2 = zeta_N^{r j1 S2}, the same for every column (a broadcast read), so a
+// column reads S1 + 1 twist entries of which S1 are shared, instead of S1 of
+// its own from a table of n S entries.
 template <class T>
-__device__ __forceinline__ T split_twist(const T* twr, T tb, int j1, int j2, int S2) {
-#if HD_TWF
-    (void)j2;
+__device__ __forceinline__ T split_twist(const T* twr, T tb, int j1, int S2) {
     return j1 == 0 ? tb : cmul(tb, ldtw(twr + (int64_t)j1 * S2));
-#else
-    (void)tb;
-    return ldtw(twr + (int64_t)j1 * S2 + j2);
-#endif
 }
 
 // Forward column j2 of residue r of input aa of instance inst.
@@ -98,11 +94,11 @@ __device__ __forceinline__ void split_colfwd_body(const SplitArgs& a, int64_t in
         const int j = j1 * a.S2 + j2;
         T b0, b1;
         load_fold<KIND, true>(f, j, a.S, ca, true, b0, b1);
-        v[j1] = cmul(cadd(b0, cmul(cr, b1)), split_twist(twr, tb, j1, j2, a.S2));
+        v[j1] = cmul(cadd(b0, cmul(cr, b1)), split_twist(twr, tb, j1, a.S2));
     }
     dft_small<S1, false>(v);
     T tw[S1];
-    power_row_twiddles<S1, HD_TWP != 0>(twS + j2, a.S2, tw);   // zeta_S^{j2 k1}
+    power_row_twiddles<S1, true>(twS + j2, a.S2, tw);   // zeta_S^{j2 k1}
     T* w = static_cast<T*>(a.work) + ((inst * a.A + aa) * a.nr + (r - a.r0)) * (int64_t)a.S;
 #pragma unroll
     for (int k1 = 0; k1 < S1; ++k1) {
@@ -139,7 +135,7 @@ __device__ __forceinline__ void split_colfwd_multi(const SplitArgs& a, int64_t i
             const int j = j1 * a.S2 + j2;
             T b0, b1;
             load_fold<KIND, true>(f, j, a.S, ca, true, b0, b1);
-            v[u][j1] = cmul(cadd(b0, cmul(cr, b1)), split_twist(twr, tb, j1, j2, a.S2));
+            v[u][j1] = cmul(cadd(b0, cmul(cr, b1)), split_twist(twr, tb, j1, a.S2));
         }
     }
     T* w = static_cast<T*>(a.work) + ((inst * a.A + aa) * a.nr + (r - a.r0)) * (int64_t)a.S;
@@ -148,7 +144,7 @@ __device__ __forceinline__ void split_colfwd_multi(const SplitArgs& a, int64_t i
         const int j2 = j2base + u * jstep;
         dft_small<S1, false>(v[u]);
         T tw[S1];
-        power_row_twiddles<S1, HD_TWP != 0>(twS + j2, a.S2, tw);   // zeta_S^{j2 k1}
+        power_row_twiddles<S1, true>(twS + j2, a.S2, tw);   // zeta_S^{j2 k1}
 #pragma unroll
         for (int k1 = 0; k1 < S1; ++k1) {
             const T t = k1 == 0 ? v[u][0] : cmul(v[u][k1], tw[k1]);
@@ -279,7 +275,7 @@ __device__ __forceinline__ void split_colbwd_body(const SplitArgs& a, int64_t in
         T cr = ldtw(twR + (int64_t)a.n * a.S + r);
         if constexpr (KIND != KIND_COMPLEX) cr = cconj(cr);
         T v[S1], tw[S1];
-        power_row_twiddles<S1, HD_TWP != 0>(twS + j2, a.S2, tw);   // zeta_S^{j2 k1}
+        power_row_twiddles<S1, true>(twS + j2, a.S2, tw);   // zeta_S^{j2 k1}
 #pragma unroll
         for (int k1 = 0; k1 < S1; ++k1) {
             const T z = base[(int64_t)(r - a.r0) * a.S + (int64_t)k1 * a.S2 + j2];
@@ -290,7 +286,7 @@ __device__ __forceinline__ void split_colbwd_body(const SplitArgs& a, int64_t in
         const T tb = ldtw(twr + j2);                  // zeta_N^{r j2}
 #pragma unroll
         for (int j1 = 0; j1 < S1; ++j1) {
-            T y = cmulc(v[j1], split_twist(twr, tb, j1, j2, a.S2));
+            T y = cmulc(v[j1], split_twist(twr, tb, j1, a.S2));
             acc_add<R, COMP>(s0[2 * j1], COMP ? c0[2 * j1] : dummy, y.x);
             acc_add<R, COMP>(s0[2 * j1 + 1], COMP ? c0[2 * j1 + 1] : dummy, y.y);
             if constexpr (NB == 2) {
@@ -363,14 +359,14 @@ __device__ __forceinline__ void split_colbwd_multi(const SplitArgs& a, int64_t i
         for (int u = 0; u < U; ++u) {
             const int j2 = j2base + u * jstep;
             T tw[S1];
-            power_row_twiddles<S1, HD_TWP != 0>(twS + j2, a.S2, tw);   // zeta_S^{j2 k1}
+            power_row_twiddles<S1, true>(twS + j2, a.S2, tw);   // zeta_S^{j2 k1}
 #pragma unroll
             for (int k1 = 1; k1 < S1; ++k1) v[u][k1] = cmulc(v[u][k1], tw[k1]);
             dft_small<S1, true>(v[u]);
             const T tb = ldtw(twr + j2);              // zeta_N^{r j2}
 #pragma unroll
             for (int j1 = 0; j1 < S1; ++j1) {
-                T y = cmulc(v[u][j1], split_twist(twr, tb, j1, j2, a.S2));
+                T y = cmulc(v[u][j1], split_twist(twr, tb, j1, a.S2));
                 acc_add<R, COMP>(s0[u][2 * j1], COMP ? c0[u][2 * j1] : dummy, y.x);
                 acc_add<R, COMP>(s0[u][2 * j1 + 1], COMP ? c0[u][2 * j1 + 1] : dummy, y.y);
                 if constexpr (NB == 2) {
