@@ -78,8 +78,17 @@ enum { HD_F32 = 0, HD_F64 = 1 };
  * term in Basdevant's form (Section 9 counts A = 3, B = 5).  Binary bound; 1D
  * plans (fused kernel: the five residue sums live in shared memory, so FP32
  * transforms up to S = 1024 and FP64 up to 512 for short rows) and 2D/3D
- * plans; no split path. */
-enum { HD_MULT_PRODUCT = 0, HD_MULT_SUM_PAIRS3 = 1, HD_MULT_BASDEVANT2 = 2, HD_MULT_BASDEVANT3 = 3 };
+ * plans; no split path.
+ * HD_MULT_MHD3: A = 6, B = 8: from the Elsasser components z+ = u + b
+ * (inputs 0, 1, 2) and z- = u - b (inputs 3, 4, 5) of a 3D incompressible
+ * magnetohydrodynamic flow, the eight entries of the traceless part of the
+ * flux tensor T_ij = z-_i z+_j: T_01, T_02, T_10, T_12, T_20, T_21,
+ * T_00 - T_22, T_11 - T_22 (Section 9 counts A = 6, B = 8 without giving the
+ * form; the trace, like that of Basdevant's velocity tensor, goes into the
+ * pressure).  Binary bound; 1D plans (fused kernel: the eight residue sums
+ * live in shared memory, so FP32 transforms up to S = 1024 and FP64 up to 512
+ * for short rows) and 2D/3D plans; no split path. */
+enum { HD_MULT_PRODUCT = 0, HD_MULT_SUM_PAIRS3 = 1, HD_MULT_BASDEVANT2 = 2, HD_MULT_BASDEVANT3 = 3, HD_MULT_MHD3 = 4 };
 
 typedef struct hd_plan hd_plan;
 
@@ -145,7 +154,7 @@ hd_status hd_derive_params(int kind, int64_t L, int64_t M, int64_t m, int64_t* p
 int64_t hd_dealias_bound(int kind, int mult, int64_t L);
 
 /* 1D complex FP32 plan.  (A, B) = (2, 1) selects HD_MULT_PRODUCT, (3, 1)
- * HD_MULT_SUM_PAIRS3, (2, 2) HD_MULT_BASDEVANT2, (3, 5) HD_MULT_BASDEVANT3; other (A, B) are
+ * HD_MULT_SUM_PAIRS3, (2, 2) HD_MULT_BASDEVANT2, (3, 5) HD_MULT_BASDEVANT3, (6, 8) HD_MULT_MHD3; other (A, B) are
  * HD_ERR_INVALID.  m = 0 selects parameters automatically
  * (tuned cache, learned selector, else a cost model); nonzero m, p, q are
  * validated: p m >= L, q m >= M, and p > 2 requires q % p == 0 (complex).

@@ -25,9 +25,19 @@ convolution:
   "sum_pairs3"  A=3, B=1:  F1F2 + F2F3 + F3F1       -> f1*f2 + f2*f3 + f3*f1
   "basdevant2"  A=2, B=2:  (F1F2, F1^2 - F2^2)      -> (f1*f2, f1*f1 - f2*f2)
   "basdevant3"  A=3, B=5:  (F1F2, F2F3, F3F1, F1^2 - F3^2, F2^2 - F3^2)
+  "mhd3"        A=6, B=8:  inputs the Elsasser components (Z+_0, Z+_1, Z+_2,
+                Z-_0, Z-_1, Z-_2); outputs the eight entries of the traceless
+                part of T_ij = Z-_i Z+_j: T_01, T_02, T_10, T_12, T_20, T_21,
+                T_00 - T_22, T_11 - T_22
 The Basdevant products are the nonlinear terms of incompressible
 Navier-Stokes in Basdevant's form, which Section 9 counts as A = B = 2 in two
-dimensions and A = 3, B = 5 in three (inputs: the velocity components).  With
+dimensions and A = 3, B = 5 in three (inputs: the velocity components).
+Section 9 gives A = 6, B = 8 for incompressible 3D magnetohydrodynamics
+without the form; "mhd3" is the reading that yields those counts: in
+Elsasser variables z+- = u +- b the nonlinear term is the divergence of the
+flux tensor z-_i z+_j, whose trace (like the velocity tensor's in
+Basdevant's form) is absorbed by the pressure gradient, leaving 9 - 1 = 8
+independent products of the 6 transformed components.  With
 B > 1 the functions below return the B outputs stacked on a new first axis.
 On integer-valued inputs every product and partial sum is an integer below
 2^53, so these FP64 sums are exact.
@@ -45,6 +55,9 @@ MULT_TERMS = {
     "sum_pairs3": (3, [[(0, 1, 1), (1, 2, 1), (2, 0, 1)]]),
     "basdevant2": (2, [[(0, 1, 1)], [(0, 0, 1), (1, 1, -1)]]),
     "basdevant3": (3, [[(0, 1, 1)], [(1, 2, 1)], [(2, 0, 1)], [(0, 0, 1), (2, 2, -1)], [(1, 1, 1), (2, 2, -1)]]),
+    # T_ij = z-_i z+_j with z+_j = f_j and z-_i = f_{3+i}
+    "mhd3": (6, [[(3, 1, 1)], [(3, 2, 1)], [(4, 0, 1)], [(4, 2, 1)], [(5, 0, 1)], [(5, 1, 1)],
+                 [(3, 0, 1), (5, 2, -1)], [(4, 1, 1), (5, 2, -1)]]),
 }
 MULTS = {k: v[0] for k, v in MULT_TERMS.items()}             # inputs A
 OUTPUTS = {k: len(v[1]) for k, v in MULT_TERMS.items()}      # outputs B

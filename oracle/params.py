@@ -53,13 +53,13 @@ def dealias_bound(kind: str, L: int, mult: str = "product") -> int:
     """Smallest M for which the returned L outputs carry no aliases.
 
     complex:   2L-1 (Section 2: M = sum L_i - (A-1) for a binary product; the
-               sum of pairwise products, and the Basdevant outputs, which
-               are signed sums of binary products, have the same bound).
+               sum of pairwise products, and the Basdevant and MHD outputs,
+               which are signed sums of binary products, have the same bound).
     centered:  L + floor(L/2): outputs c in [-H, L-H-1] with H = floor(L/2)
                receive no wrapped term when M >= L + H.
     hermitian: the centered bound of the odd expanded length 2 ceil(L/2) - 1.
     """
-    if mult not in ("product", "sum_pairs3", "basdevant2", "basdevant3"):
+    if mult not in ("product", "sum_pairs3", "basdevant2", "basdevant3", "mhd3"):
         raise ValueError(mult)
     if kind == "complex":
         return 2 * L - 1

@@ -262,6 +262,9 @@ def _mult(Fs, mult):
     if mult == "basdevant3":
         u, v, w = Fs
         return [u * v, v * w, w * u, u * u - w * w, v * v - w * w]
+    if mult == "mhd3":   # traceless part of T_ij = Z-_i Z+_j (Elsasser components)
+        p0, p1, p2, m0, m1, m2 = Fs
+        return [m0 * p1, m0 * p2, m1 * p0, m1 * p2, m2 * p0, m2 * p1, m0 * p0 - m2 * p2, m1 * p1 - m2 * p2]
     raise ValueError(mult)
 
 

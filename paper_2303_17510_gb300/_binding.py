@@ -24,16 +24,16 @@ lib = ctypes.CDLL(LIB_PATH)
 
 KIND = {"complex": 0, "centered": 1, "hermitian": 2}
 DTYPE = {"f32": 0, "f64": 1}
-MULT = {"product": 0, "sum_pairs3": 1, "basdevant2": 2, "basdevant3": 3}
+MULT = {"product": 0, "sum_pairs3": 1, "basdevant2": 2, "basdevant3": 3, "mhd3": 4}
 PLAN_NO_WORK_BUFFER = 1   # HD_PLAN_NO_WORK_BUFFER
-MULT_AB = {"product": (2, 1), "sum_pairs3": (3, 1), "basdevant2": (2, 2), "basdevant3": (3, 5)}   # inputs A, outputs B
+MULT_AB = {"product": (2, 1), "sum_pairs3": (3, 1), "basdevant2": (2, 2), "basdevant3": (3, 5), "mhd3": (6, 8)}   # inputs A, outputs B
 
 
 def _mult_of(A, B, mult):
     """The mult name (from (A, B) when not given) and B (from the mult when
     not given); the library validates the counts against the mult."""
     if mult is None:
-        mult = {2: "basdevant2", 5: "basdevant3"}.get(B) or ("product" if A == 2 else "sum_pairs3")
+        mult = {2: "basdevant2", 5: "basdevant3", 8: "mhd3"}.get(B) or ("product" if A == 2 else "sum_pairs3")
     if B is None:
         B = MULT_AB[mult][1]
     return mult, A, B

@@ -142,7 +142,6 @@ int64_t split_rows(int dtype) { return max_fused_S(dtype); }
 bool split_supported(int dtype, int kind, int mult, int64_t S, int nb) {
     (void)kind;
     (void)nb;
-    if (mult == HD_MULT_BASDEVANT2 || mult == HD_MULT_BASDEVANT3) return false;   // the split row kernels have one output
     const int64_t S2 = split_rows(dtype);
     if (!is_pow2(S) || S <= max_fused_S(dtype)) return false;
     const int64_t S1 = S / S2;
@@ -206,7 +205,8 @@ hd_status validate_axis(int kind, int mult, int64_t L, int64_t M, int64_t m, int
 // Two CTAs per SM (128 registers) for FP32 transforms up to 2048; the
 // two-output mult holds twice the residue sums and keeps 255 registers.
 int default_minb(int dtype, int64_t S, int mult) {
-    return (dtype == HD_F32 && S <= 2048 && mult != HD_MULT_BASDEVANT2 && mult != HD_MULT_BASDEVANT3) ? 2 : 1;
+    return (dtype == HD_F32 && S <= 2048 && mult != HD_MULT_BASDEVANT2 && mult != HD_MULT_BASDEVANT3 &&
+            mult != HD_MULT_MHD3) ? 2 : 1;
 }
 
 bool fused_supported(int dtype, int kind, int mult, int64_t S, int nb, int64_t Ls, bool comp, int E, int minb) {
@@ -223,10 +223,12 @@ bool cluster_supported(int dtype, int kind, int mult, int64_t S, int nb, int64_t
 
 bool mult_counts_ok(int mult, int A, int B) {
     return (mult == HD_MULT_PRODUCT && A == 2 && B == 1) || (mult == HD_MULT_SUM_PAIRS3 && A == 3 && B == 1) ||
-           (mult == HD_MULT_BASDEVANT2 && A == 2 && B == 2) || (mult == HD_MULT_BASDEVANT3 && A == 3 && B == 5);
+           (mult == HD_MULT_BASDEVANT2 && A == 2 && B == 2) || (mult == HD_MULT_BASDEVANT3 && A == 3 && B == 5) ||
+           (mult == HD_MULT_MHD3 && A == 6 && B == 8);
 }
 
 int kernel_mult(int mult) {
+    if (mult == HD_MULT_MHD3) return MULT_MHD3;
     if (mult == HD_MULT_BASDEVANT3) return MULT_BASD3;
     return mult == HD_MULT_BASDEVANT2 ? MULT_BASD2 : (mult == HD_MULT_SUM_PAIRS3 ? MULT_PAIRS3 : MULT_PRODUCT);
 }
@@ -249,6 +251,16 @@ namespace hd {
 
 #define HD_SEL(fn, c, ...)                                                                   \
     do {                                                                                     \
+        if (c.mult == MULT_MHD3) {                                                           \
+            if (c.dtype == HD_F32) {                                                         \
+                if (c.kind == KIND_COMPLEX) return fn##_f32_complex_b8(__VA_ARGS__);         \
+                if (c.kind == KIND_CENTERED) return fn##_f32_centered_b8(__VA_ARGS__);       \
+                return fn##_f32_hermitian_b8(__VA_ARGS__);                                   \
+            }                                                                                \
+            if (c.kind == KIND_COMPLEX) return fn##_f64_complex_b8(__VA_ARGS__);             \
+            if (c.kind == KIND_CENTERED) return fn##_f64_centered_b8(__VA_ARGS__);           \
+            return fn##_f64_hermitian_b8(__VA_ARGS__);                                       \
+        }                                                                                    \
         if (c.mult == MULT_BASD3) {                                                          \
             if (c.dtype == HD_F32) {                                                         \
                 if (c.kind == KIND_COMPLEX) return fn##_f32_complex_b5(__VA_ARGS__);         \
@@ -308,7 +320,7 @@ hd_status hd_device_status(void) {
         cudaGetLastError();
         return HD_ERR_CUDA;
     }
-    const int e[18] = {conv1d_take_error_f32_complex(),     conv1d_take_error_f32_centered(),
+    const int e[24] = {conv1d_take_error_f32_complex(),     conv1d_take_error_f32_centered(),
                        conv1d_take_error_f32_hermitian(),   conv1d_take_error_f64_complex(),
                        conv1d_take_error_f64_centered(),    conv1d_take_error_f64_hermitian(),
                        conv1d_take_error_f32_complex_b2(),  conv1d_take_error_f32_centered_b2(),
@@ -316,7 +328,10 @@ hd_status hd_device_status(void) {
                        conv1d_take_error_f64_centered_b2(), conv1d_take_error_f64_hermitian_b2(),
                        conv1d_take_error_f32_complex_b5(),  conv1d_take_error_f32_centered_b5(),
                        conv1d_take_error_f32_hermitian_b5(), conv1d_take_error_f64_complex_b5(),
-                       conv1d_take_error_f64_centered_b5(), conv1d_take_error_f64_hermitian_b5()};
+                       conv1d_take_error_f64_centered_b5(), conv1d_take_error_f64_hermitian_b5(),
+                       conv1d_take_error_f32_complex_b8(),  conv1d_take_error_f32_centered_b8(),
+                       conv1d_take_error_f32_hermitian_b8(), conv1d_take_error_f64_complex_b8(),
+                       conv1d_take_error_f64_centered_b8(), conv1d_take_error_f64_hermitian_b8()};
     hd_status st = HD_OK;
     for (int v : e) {
         if (v < 0) return HD_ERR_CUDA;
@@ -368,7 +383,7 @@ hd_status hd_derive_params(int kind, int64_t L, int64_t M, int64_t m, int64_t* p
 int64_t hd_dealias_bound(int kind, int mult, int64_t L) {
     // every output of every mult is a (signed) sum of binary products
     if (L <= 0 || (mult != HD_MULT_PRODUCT && mult != HD_MULT_SUM_PAIRS3 && mult != HD_MULT_BASDEVANT2 &&
-                   mult != HD_MULT_BASDEVANT3))
+                   mult != HD_MULT_BASDEVANT3 && mult != HD_MULT_MHD3))
         return -1;
     if (kind == HD_COMPLEX) return 2 * L - 1;
     if (kind == HD_CENTERED) return L + L / 2;
@@ -383,7 +398,8 @@ hd_status hd_plan_create(hd_plan** out, int64_t L, int64_t M, int A, int B, int6
                          int D) {
     if (!out) return HD_ERR_INVALID;
     *out = nullptr;
-    if (!((A == 2 && (B == 1 || B == 2)) || (A == 3 && B == 1))) return HD_ERR_INVALID;
+    const int mult = B == 8 ? HD_MULT_MHD3 : (B == 5 ? HD_MULT_BASDEVANT3 : (B == 2 ? HD_MULT_BASDEVANT2 : (A == 2 ? HD_MULT_PRODUCT : HD_MULT_SUM_PAIRS3)));
+    if (!hd::mult_counts_ok(mult, A, B)) return HD_ERR_INVALID;
     hd_desc d;
     std::memset(&d, 0, sizeof(d));
     d.ndim = 1;
@@ -393,7 +409,7 @@ hd_status hd_plan_create(hd_plan** out, int64_t L, int64_t M, int A, int B, int6
     d.B = B;
     d.kind = HD_COMPLEX;
     d.dtype = HD_F32;
-    d.mult = B == 5 ? HD_MULT_BASDEVANT3 : (B == 2 ? HD_MULT_BASDEVANT2 : (A == 2 ? HD_MULT_PRODUCT : HD_MULT_SUM_PAIRS3));
+    d.mult = mult;
     d.m[0] = m;
     d.p[0] = p;
     d.q[0] = q;
@@ -479,7 +495,7 @@ hd_status hd_forward_residue(const hd_plan* plan, const void* f, int64_t r, void
     const hd::AxisPlan& ax = plan->ax[0];
     if (r < 0 || r >= ax.n) return HD_ERR_INVALID;
     if (ax.path != hd::PATH_FUSED) return HD_ERR_UNSUPPORTED;
-    const void* fin[3] = {f, f, f};
+    const void* fin[kMaxIn] = {f, f, f, f, f, f};
     ConvArgs a = hd::make_conv_args(*plan, ax, 1, fin, nullptr, 0);
     Conv1dCfg c = hd::fused_cfg(*plan, ax);
     cudaError_t e = hd::forward_residue_launch(c, a, (int)r, (int)ax.m, outp, (cudaStream_t)stream);

@@ -22,7 +22,7 @@
 namespace hd {
 
 struct ColArgs {
-    const void* f[3];     // colfwd: A input bases; element (inst, x, col) at f + inst*inst_stride + x*pitch + col
+    const void* f[kMaxIn];   // colfwd: A input bases; element (inst, x, col) at f + inst*inst_stride + x*pitch + col
     void* work;           // F[a][inst][r'][slot][col]
     void* h[kMaxOut];     // colbwd: B output bases, same layout as the inputs
     int64_t inst_stride;  // elements between outer instances
@@ -93,9 +93,10 @@ __global__ void __launch_bounds__(ColShape<S, E>::THREADS) col_forward(const __g
         } else {
             T cr = ldtw(twN + (int64_t)a.n * S + r);
             if constexpr (KIND == KIND_CENTERED) cr = cconj(cr);
+            const TwistRow tr = twist_row(r, a.n);   // conjugate symmetry
 #pragma unroll
             for (int e = 0; e < E; ++e)
-                v[e] = cmul(cadd(b0[e], cmul(cr, b1[e])), ldtw(twN + (int64_t)r * S + tau + TT * e));
+                v[e] = cmul(cadd(b0[e], cmul(cr, b1[e])), twist_ld(twN + (int64_t)tr.row * S + tau + TT * e, tr.conj));
         }
         fft_forward<S, E, 1, TY>(v, sm, tw, tau);
         if (valid) {
@@ -143,10 +144,11 @@ __global__ void __launch_bounds__(ColShape<S, E>::THREADS) col_backward(const __
         for (int e = 0; e < E; ++e) v[e] = valid ? ld_in<true>(g, (int64_t)(tau + TT * e) * a.ncols) : czero<T>();
         fft_inverse<S, E, 1, TY>(v, sm, tw, tau);
         const bool r0 = r == 0;   // unit twists
+        const TwistRow tr = twist_row(r, a.n);   // conjugate symmetry
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             const int j = tau + TT * e;
-            const T yv = r0 ? v[e] : cmulc(v[e], ldtw(twN + (int64_t)r * S + j));
+            const T yv = r0 ? v[e] : cmulc(v[e], twist_ld(twN + (int64_t)tr.row * S + j, tr.conj));
             acc_add<R, COMP>(s0[2 * e], COMP ? c0[2 * e] : dummy, yv.x);
             acc_add<R, COMP>(s0[2 * e + 1], COMP ? c0[2 * e + 1] : dummy, yv.y);
             const T y1 = r0 ? yv : cmulc(yv, cr);

@@ -44,7 +44,7 @@
 namespace hd {
 
 enum { KIND_COMPLEX = 0, KIND_CENTERED = 1, KIND_HERMITIAN = 2 };
-enum { MULT_PRODUCT = 0, MULT_PAIRS3 = 1, MULT_BASD2 = 2, MULT_BASD3 = 3 };
+enum { MULT_PRODUCT = 0, MULT_PAIRS3 = 1, MULT_BASD2 = 2, MULT_BASD3 = 3, MULT_MHD3 = 4 };
 
 // Inputs A and outputs B of each mult; NX exchange buffers.
 //   MULT_PRODUCT  A = 2, B = 1:  F1 F2
@@ -54,6 +54,10 @@ enum { MULT_PRODUCT = 0, MULT_PAIRS3 = 1, MULT_BASD2 = 2, MULT_BASD3 = 3 };
 //                 (velocity components in; Section 9 counts A = B = 2)
 //   MULT_BASD3    A = 3, B = 5:  (F1 F2, F2 F3, F3 F1, F1^2 - F3^2, F2^2 - F3^2),
 //                 the same for 3D (Section 9 counts A = 3, B = 5)
+//   MULT_MHD3     A = 6, B = 8:  inputs the Elsasser components Z+_0..2, Z-_0..2;
+//                 outputs the traceless part of T_ij = Z-_i Z+_j: T_01, T_02,
+//                 T_10, T_12, T_20, T_21, T_00 - T_22, T_11 - T_22 (3D
+//                 incompressible MHD, which Section 9 counts as A = 6, B = 8)
 // With B <= 2 the residue sums live in registers and the B inverse
 // transforms run together (NX = max(A, B) buffers).  With more outputs
 // (OUT_SMEM) the sums live in shared memory, ACC = B * 2 * S values per group
@@ -61,13 +65,14 @@ enum { MULT_PRODUCT = 0, MULT_PAIRS3 = 1, MULT_BASD2 = 2, MULT_BASD3 = 3 };
 // output at a time from the forward spectra kept in registers (NX = A).
 template <int MULT>
 struct MultShape {
-    static constexpr int A = (MULT == MULT_PAIRS3 || MULT == MULT_BASD3) ? 3 : 2;
-    static constexpr int B = MULT == MULT_BASD2 ? 2 : (MULT == MULT_BASD3 ? 5 : 1);
+    static constexpr int A = MULT == MULT_MHD3 ? 6 : ((MULT == MULT_PAIRS3 || MULT == MULT_BASD3) ? 3 : 2);
+    static constexpr int B = MULT == MULT_BASD2 ? 2 : (MULT == MULT_BASD3 ? 5 : (MULT == MULT_MHD3 ? 8 : 1));
     static constexpr bool OUT_SMEM = B > 2;
     static constexpr int NX = OUT_SMEM ? A : (A > B ? A : B);
     __host__ __device__ static constexpr int acc(int S) { return OUT_SMEM ? B * 2 * S : 0; }
 };
-constexpr int kMaxOut = 5;
+constexpr int kMaxOut = 8;
+constexpr int kMaxIn = 6;
 
 // arithmetic of mult on complex or real values
 __device__ __forceinline__ float xmul(float a, float b) { return a * b; }
@@ -94,32 +99,59 @@ __device__ __forceinline__ void mult_point(const X* x, X* y) {
     } else if constexpr (MULT == MULT_BASD2) {     // F1 F2, F1^2 - F2^2 = (F1 + F2)(F1 - F2)
         y[0] = xmul(x[0], x[XS]);
         y[YS] = xmul(xadd(x[0], x[XS]), xsub(x[0], x[XS]));
-    } else {
-        static_assert(MULT == MULT_BASD3, "mult");
+    } else if constexpr (MULT == MULT_BASD3) {
         y[0] = xmul(x[0], x[XS]);
         y[YS] = xmul(x[XS], x[2 * XS]);
         y[2 * YS] = xmul(x[2 * XS], x[0]);
         y[3 * YS] = xmul(xadd(x[0], x[2 * XS]), xsub(x[0], x[2 * XS]));
         y[4 * YS] = xmul(xadd(x[XS], x[2 * XS]), xsub(x[XS], x[2 * XS]));
+    } else {
+        static_assert(MULT == MULT_MHD3, "mult");
+        // z+_j = x[j XS], z-_i = x[(3 + i) XS]; T_ij = z-_i z+_j, traceless part
+        const X p0 = x[0], p1 = x[XS], p2 = x[2 * XS], m0 = x[3 * XS], m1 = x[4 * XS], m2 = x[5 * XS];
+        const X t22 = xmul(m2, p2);
+        y[0] = xmul(m0, p1);
+        y[YS] = xmul(m0, p2);
+        y[2 * YS] = xmul(m1, p0);
+        y[3 * YS] = xmul(m1, p2);
+        y[4 * YS] = xmul(m2, p0);
+        y[5 * YS] = xmul(m2, p1);
+        y[6 * YS] = xsub(xmul(m0, p0), t22);
+        y[7 * YS] = xsub(xmul(m1, p1), t22);
     }
 }
 
 // output b of mult at one point (the OUT_SMEM path, one output at a time)
 template <int MULT, int XS, class X>
 __device__ __forceinline__ X mult_out(const X* x, int b) {
-    static_assert(MULT == MULT_BASD3, "outputs one at a time: the 3D Basdevant mult");
-    const X x0 = x[0], x1 = x[XS], x2 = x[2 * XS];
-    switch (b) {
-        case 0: return xmul(x0, x1);
-        case 1: return xmul(x1, x2);
-        case 2: return xmul(x2, x0);
-        case 3: return xmul(xadd(x0, x2), xsub(x0, x2));
-        default: return xmul(xadd(x1, x2), xsub(x1, x2));
+    static_assert(MULT == MULT_BASD3 || MULT == MULT_MHD3, "outputs one at a time: the 3D Basdevant and MHD mults");
+    if constexpr (MULT == MULT_BASD3) {
+        const X x0 = x[0], x1 = x[XS], x2 = x[2 * XS];
+        switch (b) {
+            case 0: return xmul(x0, x1);
+            case 1: return xmul(x1, x2);
+            case 2: return xmul(x2, x0);
+            case 3: return xmul(xadd(x0, x2), xsub(x0, x2));
+            default: return xmul(xadd(x1, x2), xsub(x1, x2));
+        }
+    } else {
+        // z+_j = x[j XS], z-_i = x[(3 + i) XS]; T_ij = z-_i z+_j
+        const X p0 = x[0], p1 = x[XS], p2 = x[2 * XS], m0 = x[3 * XS], m1 = x[4 * XS], m2 = x[5 * XS];
+        switch (b) {
+            case 0: return xmul(m0, p1);
+            case 1: return xmul(m0, p2);
+            case 2: return xmul(m1, p0);
+            case 3: return xmul(m1, p2);
+            case 4: return xmul(m2, p0);
+            case 5: return xmul(m2, p1);
+            case 6: return xsub(xmul(m0, p0), xmul(m2, p2));
+            default: return xsub(xmul(m1, p1), xmul(m2, p2));
+        }
     }
 }
 
 struct ConvArgs {
-    const void* f[3];   // A input bases (device)
+    const void* f[kMaxIn];   // A input bases (device)
     void* h[kMaxOut];   // B output bases (device)
     int64_t stride;     // elements between instances
     int64_t count;      // instances
@@ -141,6 +173,30 @@ template <bool B>
 struct BoolTag {
     static constexpr bool value = B;
 };
+
+// Conjugate symmetry of the twists (Section 6.3).  Residues r and n - r have
+// conjugate twists up to a factor zeta_S^{j}: zeta_N^{(n-r) j} = zeta_S^{j}
+// conj(zeta_N^{r j}), since N = n S.  So residue r > n/2 reads the twist row of
+// residue n - r and conjugates it; its transform input is then the true one
+// times zeta_S^{-j}, whose FFT is the true spectrum shifted by one frequency
+// (F'_k = F_{k-1}).  All A inputs shift alike, so the pointwise mult gives the
+// shifted product, and the backward transform with the same conjugated twist
+// (the conjugate of zeta_S^{-j} conj(zeta_N^{r' j})) puts the contribution back
+// in place: zeta_N^{-r' i} IFFT(P)_i = zeta_N^{(n-r') i} IFFT(P')_i.  Residue
+// n/2 (even n) pairs with itself and keeps its own row.  Half of the n twist
+// rows are read; the block-1 factor zeta_N^{r S} is unchanged.
+struct TwistRow {
+    int row;     // residue whose table row is read
+    bool conj;   // conjugate the entries
+};
+__host__ __device__ __forceinline__ TwistRow twist_row(int r, int n) {
+    return 2 * r > n ? TwistRow{n - r, true} : TwistRow{r, false};
+}
+template <class T>
+__device__ __forceinline__ T twist_ld(const T* p, bool conj) {
+    const T w = ldtw(p);
+    return conj ? cconj(w) : w;
+}
 
 // Residue-sum accumulation.  COMP: TwoSum compensated s + c += x (FP32 path);
 // otherwise a plain sum.
@@ -274,14 +330,15 @@ __device__ __forceinline__ void conv1d_body(const ConvArgs& a, int64_t inst, boo
         // residue r; R0: r = 0, whose twists are all 1 (no loads, no multiplies)
         auto residue = [&](int r, auto r0_tag) {
             constexpr bool R0 = decltype(r0_tag)::value;
-            const T* twr = twN + (int64_t)r * S;        // zeta_N^{r j}, j < S
+            const TwistRow tr = twist_row(r, a.n);
+            const T* twr = twN + (int64_t)tr.row * S;   // zeta_N^{r j}, j < S (or the paired row, conjugated)
             T cr = R0 ? mk<T>(1, 0) : ldtw(twN + (int64_t)a.n * S + r);    // zeta_N^{r S}
             if constexpr (KIND == KIND_CENTERED) cr = cconj(cr);
             T v[A * E];
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const int j = tau + TT * e;
-                const T tw = R0 ? mk<T>(1, 0) : ldtw(twr + j);
+                const T tw = R0 ? mk<T>(1, 0) : twist_ld(twr + j, tr.conj);
 #pragma unroll
                 for (int aa = 0; aa < A; ++aa) {
                     if constexpr (KIND == KIND_COMPLEX && NB == 1) {
@@ -301,7 +358,7 @@ __device__ __forceinline__ void conv1d_body(const ConvArgs& a, int64_t inst, boo
             if constexpr (OSM) {
                 T twe[E];
 #pragma unroll
-                for (int e = 0; e < E; ++e) twe[e] = R0 ? mk<T>(1, 0) : ldtw(twr + tau + TT * e);
+                for (int e = 0; e < E; ++e) twe[e] = R0 ? mk<T>(1, 0) : twist_ld(twr + tau + TT * e, tr.conj);
 #pragma unroll 1
                 for (int b = 0; b < B; ++b) {
                     T p[E];
@@ -329,7 +386,7 @@ __device__ __forceinline__ void conv1d_body(const ConvArgs& a, int64_t inst, boo
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const int j = tau + TT * e;
-                const T tw = R0 ? mk<T>(1, 0) : ldtw(twr + j);
+                const T tw = R0 ? mk<T>(1, 0) : twist_ld(twr + j, tr.conj);
 #pragma unroll
                 for (int b = 0; b < B; ++b) {
                     const int o = b * 2 * E + 2 * e;
@@ -726,8 +783,9 @@ __global__ void __launch_bounds__(S / E) conv1d_cluster_kernel(const __grid_cons
             // this residue's twists zeta_N^{r j}, once every thread has finished
             // the previous residue's accumulation (which reads the old row)
             __syncthreads();
-            const T* row = twN + (int64_t)r * S;
-            for (int i = tau; i < S; i += TT) twr[i] = __ldg(row + i);
+            const TwistRow tr = twist_row(r, a.n);   // conjugate symmetry (see twist_row)
+            const T* row = twN + (int64_t)tr.row * S;
+            for (int i = tau; i < S; i += TT) twr[i] = twist_ld(row + i, tr.conj);
             __syncthreads();
 #pragma unroll
             for (int e = 0; e < E; ++e) {

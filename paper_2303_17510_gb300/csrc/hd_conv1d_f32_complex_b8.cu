@@ -1,0 +1,10 @@
+// Fused 1D convolution kernels: f32, complex data, the eight-output mult (3D MHD) (instantiation unit).
+#define HD_REAL float
+#define HD_KIND hd::KIND_COMPLEX
+#define HD_DT f32
+#define HD_KN complex_b8
+#define HD_VARIANTS HD_VARIANTS_F32_B8
+#define HD_CLUSTER_VARIANTS HD_CLUSTER_VARIANTS_F32
+#define HD_UNIT_MULTS(Y, ...) Y(MULT_MHD3, __VA_ARGS__)
+#include "hd_conv1d_variants.h"
+#include "hd_conv1d_tu.cuh"

@@ -19,6 +19,15 @@
     X(2, 2, 1) X(4, 4, 1) X(8, 8, 1) X(16, 8, 1) X(32, 8, 1) X(64, 8, 1) X(128, 8, 1) X(256, 8, 1) X(512, 8, 1) \
     X(1024, 8, 1)
 
+// Eight-output mult (3D MHD, six inputs): one variant per size, one CTA per SM;
+// the residue sums of the eight outputs live in shared memory (16 S values),
+// which leaves FP32 transforms of 1024 points and FP64 of 512 to short rows.
+#define HD_VARIANTS_F32_B8(X) \
+    X(2, 2, 1) X(4, 4, 1) X(8, 8, 1) X(16, 8, 1) X(32, 8, 1) X(64, 8, 1) X(128, 8, 1) X(256, 8, 1) X(512, 8, 1) \
+    X(1024, 8, 1)
+#define HD_VARIANTS_F64_B8(X) \
+    X(2, 2, 1) X(4, 4, 1) X(8, 8, 1) X(16, 8, 1) X(32, 8, 1) X(64, 8, 1) X(128, 8, 1) X(256, 8, 1) X(512, 8, 1)
+
 // Cluster variants (D > 1 residues per pass, one convolution per cluster), as X(S, E).
 // FP64 takes E = 4 and 2 as well: a CTA of S/4 or S/2 threads spreads over all
 // four SM sub-partitions (each with its own FP64 unit) with more warps to

@@ -50,7 +50,7 @@ int col_E_of_f64(int S);
 
 // per translation unit entry points (dtype x kind x mult set: the
 // single-output mults, the two-output one in the _b2 units, the five-output
-// one in the _b5 units)
+// one in the _b5 units, the eight-output one in the _b8 units)
 #define HD_DECL_TU(DT, KN)                                                                                   \
     bool conv1d_available_##DT##_##KN(const Conv1dCfg& c, int ls_pad);                                                    \
     cudaError_t conv1d_launch_##DT##_##KN(const Conv1dCfg& c, const ConvArgs& a, cudaStream_t st);            \
@@ -78,6 +78,12 @@ HD_DECL_TU(f32, hermitian_b5)
 HD_DECL_TU(f64, complex_b5)
 HD_DECL_TU(f64, centered_b5)
 HD_DECL_TU(f64, hermitian_b5)
+HD_DECL_TU(f32, complex_b8)
+HD_DECL_TU(f32, centered_b8)
+HD_DECL_TU(f32, hermitian_b8)
+HD_DECL_TU(f64, complex_b8)
+HD_DECL_TU(f64, centered_b8)
+HD_DECL_TU(f64, hermitian_b8)
 #undef HD_DECL_TU
 
 }  // namespace hd

@@ -130,7 +130,7 @@ hd_status exec_level_pass(const hd_plan& pl, int level, int64_t cnt, const void*
         // the transformed slices: A batches of cnt * nrb * S sub-arrays of ncols
         // values; the sub-convolutions write output b over part b
         const int64_t sub = cnt * nrb * ax.S;
-        const void* g[3];
+        const void* g[kMaxIn];
         void* gh[kMaxOut];
         for (int i = 0; i < pl.A; ++i) g[i] = static_cast<const char*>(pl.work[level]) + (size_t)i * sub * ncols * esz;
         for (int b = 0; b < pl.B; ++b) gh[b] = static_cast<char*>(pl.work[level]) + (size_t)b * sub * ncols * esz;
@@ -158,7 +158,7 @@ hd_status exec_level(const hd_plan& pl, int level, int64_t cnt, const void* cons
     const int64_t ch = pl.level_chunk[level] > 0 ? pl.level_chunk[level] : cnt;
     for (int64_t c0 = 0; c0 < cnt; c0 += ch) {
         const int64_t cc = cnt - c0 < ch ? cnt - c0 : ch;
-        const void* fc[3];
+        const void* fc[kMaxIn];
         void* hc[kMaxOut];
         for (int a = 0; a < pl.A; ++a) fc[a] = static_cast<const char*>(f[a]) + (size_t)(c0 * inst_stride) * esz;
         for (int b = 0; b < pl.B; ++b) hc[b] = static_cast<char*>(h[b]) + (size_t)(c0 * inst_stride) * esz;
@@ -288,7 +288,7 @@ hd_status plan_create_nd(hd_plan** out, const hd_desc* d) {
     // the innermost rows of the split path use the plan's chunked work buffer
     if (st == HD_OK && pl->ax[nd - 1].path == PATH_SPLIT) {
         AxisPlan& ax = pl->ax[nd - 1];
-        const size_t per = (size_t)d->A * (size_t)split_block(ax) * (size_t)ax.S * esz;
+        const size_t per = (size_t)(d->A > d->B ? d->A : d->B) * (size_t)split_block(ax) * (size_t)ax.S * esz;
         int64_t ch = (int64_t)((64u << 20) / per);   // as 1D plans: at most 64 MiB, L2-resident
         ax.chunk = ch < 1 ? 1 : (ch > 2048 ? 2048 : ch);
         if (cudaMalloc(&pl->scratch, per * (size_t)ax.chunk) != cudaSuccess) {
@@ -311,7 +311,7 @@ hd_status plan_execute_nd(hd_plan* pl, int64_t count, const void* const* f, void
                           int64_t r_begin, int64_t r_end, cudaStream_t st) {
     const size_t esz = pl->dtype == HD_F64 ? 16 : 8;
     for (int64_t i = 0; i < count; ++i) {
-        const void* fi[3];
+        const void* fi[kMaxIn];
         void* hi[kMaxOut];
         for (int a = 0; a < pl->A; ++a) fi[a] = static_cast<const char*>(f[a]) + (size_t)(i * stride) * esz;
         for (int b = 0; b < pl->B; ++b) hi[b] = static_cast<char*>(h[b]) + (size_t)(i * stride) * esz;

@@ -49,7 +49,7 @@ extern "C" hd_status hd_convolve_batched_noalloc(const hd_plan* plan, int64_t co
         if (!h[b]) return HD_ERR_INVALID;
     if (count > 1 && batch_stride < plan->instance_elems) return HD_ERR_INVALID;
     const size_t esz = plan->dtype == HD_F64 ? 16 : 8;
-    const size_t per = (size_t)plan->A * (size_t)hd::split_block(ax) * (size_t)ax.S * esz;
+    const size_t per = (size_t)(plan->A > plan->B ? plan->A : plan->B) * (size_t)hd::split_block(ax) * (size_t)ax.S * esz;
     if (per > HD_NOALLOC_SCRATCH_BYTES) return HD_ERR_SCRATCH_LIMIT;
     if (count == 0) return HD_OK;
     hd::DeviceGuard guard(plan->device);   // the plan's device, as hd_convolve_batched does

@@ -174,11 +174,12 @@ hd_status plan_finish(const hd_desc* d, const AxisPlan& ax, hd_plan** out) {
         st = upload_split_twiddles(a0.S1, a0.S2, d->dtype, &a0.twS);
         if (st == HD_OK) st = upload_fft_twiddles(a0.S2, a0.E, d->dtype, &a0.twS2);
         if (st == HD_OK) {
-            // work buffer of Section 5: A n S values per instance, a chunk of
-            // instances at a time, at most 64 MiB so that the round trips
-            // between the three phases stay in L2
+            // work buffer of Section 5: max(A, B) n S values per instance (the
+            // rows write output b over part b), a chunk of instances at a time,
+            // at most 64 MiB so that the round trips between the three phases
+            // stay in L2
             const size_t esz = d->dtype == HD_F64 ? 16 : 8;
-            const size_t per = (size_t)d->A * (size_t)split_block(a0) * (size_t)a0.S * esz;
+            const size_t per = (size_t)(d->A > d->B ? d->A : d->B) * (size_t)split_block(a0) * (size_t)a0.S * esz;
             int64_t ch = (int64_t)((64u << 20) / per);
             if (ch > 2048) ch = 2048;
             if (ch < 1) ch = 1;
@@ -279,7 +280,7 @@ ConvArgs make_conv_args(const hd_plan& pl, const AxisPlan& ax, int64_t count, co
                         int64_t stride) {
     ConvArgs a;
     std::memset(&a, 0, sizeof(a));
-    for (int i = 0; i < pl.A && i < 3; ++i) a.f[i] = f[i];
+    for (int i = 0; i < pl.A && i < kMaxIn; ++i) a.f[i] = f[i];
     for (int b = 0; b < pl.B && b < kMaxOut; ++b) a.h[b] = h ? h[b] : nullptr;
     a.stride = stride;
     a.count = count;
@@ -315,8 +316,8 @@ SplitArgs make_split_args(const hd_plan& pl, const AxisPlan& ax, int64_t first, 
     SplitArgs a;
     std::memset(&a, 0, sizeof(a));
     const size_t esz = pl.dtype == HD_F64 ? 16 : 8;
-    for (int i = 0; i < pl.A && i < 3; ++i) a.f[i] = static_cast<const char*>(f[i]) + first * stride * esz;
-    a.h = static_cast<char*>(h[0]) + first * stride * esz;
+    for (int i = 0; i < pl.A && i < kMaxIn; ++i) a.f[i] = static_cast<const char*>(f[i]) + first * stride * esz;
+    for (int b = 0; b < pl.B && b < kMaxOut; ++b) a.h[b] = static_cast<char*>(h[b]) + first * stride * esz;
     a.stride = stride;
     a.count = count;
     a.L = (int)ax.L;
@@ -327,6 +328,8 @@ SplitArgs make_split_args(const hd_plan& pl, const AxisPlan& ax, int64_t first, 
     a.S1 = (int)ax.S1;
     a.S2 = (int)ax.S2;
     a.A = pl.A;
+    a.B = pl.B;
+    a.P = pl.A > pl.B ? pl.A : pl.B;
     a.twS = ax.twS;
     a.twR = ax.twN;
     a.twS2 = ax.twS2;
@@ -352,7 +355,8 @@ hd_status split_execute_range(const hd_plan& pl, const AxisPlan& ax, int64_t cou
     // output, so blocked plans cannot write over their inputs
     if (r_begin + blk < r_end)
         for (int a = 0; a < pl.A; ++a)
-            if (f[a] == h[0]) return HD_ERR_INVALID;
+            for (int b = 0; b < pl.B; ++b)
+                if (f[a] == h[b]) return HD_ERR_INVALID;
     for (int64_t first = 0; first < count; first += chunk) {
         const int64_t cnt = count - first < chunk ? count - first : chunk;
         SplitArgs a = make_split_args(pl, ax, first, cnt, f, h, stride, work);

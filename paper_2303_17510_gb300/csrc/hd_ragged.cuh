@@ -112,7 +112,9 @@ __device__ __forceinline__ SplitArgs split_args_of(const RInst& r) {
     a.f[0] = r.f[0];
     a.f[1] = r.f[1];
     a.f[2] = r.f[2];
-    a.h = r.h;
+    for (int i = 3; i < kMaxIn; ++i) a.f[i] = nullptr;
+    a.h[0] = r.h;   // one output (B = 1)
+    for (int b = 1; b < kMaxOut; ++b) a.h[b] = nullptr;
     a.stride = 0;
     a.count = 1;
     a.L = r.L;
@@ -123,6 +125,8 @@ __device__ __forceinline__ SplitArgs split_args_of(const RInst& r) {
     a.S1 = r.S1;
     a.S2 = r.S2;
     a.A = r.A;
+    a.B = 1;
+    a.P = r.A;
     a.twS = r.twS;
     a.twR = r.twN;
     a.twS2 = r.twS2;
@@ -139,6 +143,7 @@ __device__ __forceinline__ ConvArgs conv_args_of(const RInst& r) {
     a.f[0] = r.f[0];
     a.f[1] = r.f[1];
     a.f[2] = r.f[2];
+    for (int i = 3; i < kMaxIn; ++i) a.f[i] = nullptr;
     a.h[0] = r.h;   // one output (B = 1)
     for (int b = 1; b < kMaxOut; ++b) a.h[b] = nullptr;
     a.stride = 0;

@@ -26,23 +26,26 @@
 // the inverse of a real spectrum is Hermitian, so y is used directly.
 #pragma once
 
+#include <type_traits>
+
 #include "hd_conv1d.cuh"
 
 namespace hd {
 
 struct SplitArgs {
-    const void* f[3];   // A input bases
-    void* h;            // output base
+    const void* f[kMaxIn];   // A input bases
+    void* h[kMaxOut];        // B output bases
     int64_t stride;     // elements between instances
     int64_t count;      // instances in this chunk
     int L, Ls, H;       // as ConvArgs
     int n;              // residues
     int S, S1, S2;      // transform size and its split
-    int A;
+    int A, B;           // inputs, outputs
+    int P;              // work-buffer parts per instance: max(A, B) (output b is written over part b)
     const void* twS;    // zeta_S^{j2 k1} at k1 S2 + j2 (k1 < S1, j2 < S2)
     const void* twR;    // residue twists (ConvArgs::twN layout)
     const void* twS2;   // FFT pass twiddles of the size-S2 row FFT
-    void* work;         // scratch: [instance][a][r - r0][k1][j2]
+    void* work;         // scratch: [instance][part < P][r - r0][k1][j2]
     double invN;
     int r0, nr;         // residue block: residues r0 .. r0 + nr - 1
     int accumulate;     // colbwd: add to the output (blocks after the first)
@@ -68,9 +71,11 @@ __device__ __forceinline__ void l2_discard(const void* p, int64_t bytes, int tid
 // j1 S2 = zeta_N^{r j1 S2}, the same for every column (a broadcast read), so a
 // column reads S1 + 1 twist entries of which S1 are shared, instead of S1 of
 // its own from a table of n S entries.
+// With conjugate symmetry (twist_row) both factors come from the paired row,
+// conjugated: tb is loaded conjugated, the shared factor here.
 template <class T>
-__device__ __forceinline__ T split_twist(const T* twr, T tb, int j1, int S2) {
-    return j1 == 0 ? tb : cmul(tb, ldtw(twr + (int64_t)j1 * S2));
+__device__ __forceinline__ T split_twist(const T* twr, T tb, int j1, int S2, bool conj) {
+    return j1 == 0 ? tb : cmul(tb, twist_ld(twr + (int64_t)j1 * S2, conj));
 }
 
 // Forward column j2 of residue r of input aa of instance inst.
@@ -86,20 +91,21 @@ __device__ __forceinline__ void split_colfwd_body(const SplitArgs& a, int64_t in
     ca.H = a.H;
     T cr = ldtw(twR + (int64_t)a.n * a.S + r);      // zeta_N^{r S}
     if constexpr (KIND != KIND_COMPLEX) cr = cconj(cr);
-    const T* twr = twR + (int64_t)r * a.S;
-    const T tb = ldtw(twr + j2);                      // zeta_N^{r j2}
+    const TwistRow tr = twist_row(r, a.n);            // conjugate symmetry
+    const T* twr = twR + (int64_t)tr.row * a.S;
+    const T tb = twist_ld(twr + j2, tr.conj);         // zeta_N^{r j2}
     T v[S1];
 #pragma unroll
     for (int j1 = 0; j1 < S1; ++j1) {
         const int j = j1 * a.S2 + j2;
         T b0, b1;
         load_fold<KIND, true>(f, j, a.S, ca, true, b0, b1);
-        v[j1] = cmul(cadd(b0, cmul(cr, b1)), split_twist(twr, tb, j1, a.S2));
+        v[j1] = cmul(cadd(b0, cmul(cr, b1)), split_twist(twr, tb, j1, a.S2, tr.conj));
     }
     dft_small<S1, false>(v);
     T tw[S1];
     power_row_twiddles<S1, true>(twS + j2, a.S2, tw);   // zeta_S^{j2 k1}
-    T* w = static_cast<T*>(a.work) + ((inst * a.A + aa) * a.nr + (r - a.r0)) * (int64_t)a.S;
+    T* w = static_cast<T*>(a.work) + ((inst * a.P + aa) * a.nr + (r - a.r0)) * (int64_t)a.S;
 #pragma unroll
     for (int k1 = 0; k1 < S1; ++k1) {
         const T t = k1 == 0 ? v[0] : cmul(v[k1], tw[k1]);
@@ -124,21 +130,22 @@ __device__ __forceinline__ void split_colfwd_multi(const SplitArgs& a, int64_t i
     ca.H = a.H;
     T cr = ldtw(twR + (int64_t)a.n * a.S + r);      // zeta_N^{r S}
     if constexpr (KIND != KIND_COMPLEX) cr = cconj(cr);
-    const T* twr = twR + (int64_t)r * a.S;
+    const TwistRow tr = twist_row(r, a.n);            // conjugate symmetry
+    const T* twr = twR + (int64_t)tr.row * a.S;
     T v[U][S1];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         const int j2 = j2base + u * jstep;
-        const T tb = ldtw(twr + j2);                  // zeta_N^{r j2}
+        const T tb = twist_ld(twr + j2, tr.conj);     // zeta_N^{r j2}
 #pragma unroll
         for (int j1 = 0; j1 < S1; ++j1) {
             const int j = j1 * a.S2 + j2;
             T b0, b1;
             load_fold<KIND, true>(f, j, a.S, ca, true, b0, b1);
-            v[u][j1] = cmul(cadd(b0, cmul(cr, b1)), split_twist(twr, tb, j1, a.S2));
+            v[u][j1] = cmul(cadd(b0, cmul(cr, b1)), split_twist(twr, tb, j1, a.S2, tr.conj));
         }
     }
-    T* w = static_cast<T*>(a.work) + ((inst * a.A + aa) * a.nr + (r - a.r0)) * (int64_t)a.S;
+    T* w = static_cast<T*>(a.work) + ((inst * a.P + aa) * a.nr + (r - a.r0)) * (int64_t)a.S;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         const int j2 = j2base + u * jstep;
@@ -168,7 +175,10 @@ __global__ void __launch_bounds__(256) split_colfwd(const __grid_constant__ Spli
 }
 
 // Row `row` (= (instance * n + r) * S1 + k1) for one group of S2/E threads;
-// sm is the group's A exchange buffers.
+// sm is the group's exchange buffers (NX of MultShape<MULT>).  The A input
+// rows are transformed together, mult forms the B output spectra (together for
+// B <= 2, one at a time with the residue spectra in registers for more), and
+// output b is written over part b of the work buffer.
 // DISCARD: drop the dead input rows a >= 1 from L2 once they are loaded (the
 // persistent ragged kernel, whose work buffers would otherwise be written back
 // to DRAM; measured slower than leaving them for the batched kernels).
@@ -178,17 +188,19 @@ __device__ __forceinline__ void split_row_body(const SplitArgs& a, int64_t row, 
     using Sh = FftShape<S2, E>;
     constexpr int TT = Sh::T;
     constexpr int A = MultShape<MULT>::A;
-    static_assert(MultShape<MULT>::B == 1, "single-output mults only");
+    constexpr int B = MultShape<MULT>::B;
+    static_assert(!DISCARD || B == 1, "dead-row discards assume one output");
     const int k1 = (int)(row % a.S1);
     const int64_t rr = row / a.S1;
     const int rb = (int)(rr % a.nr);   // residue a.r0 + rb
     const int64_t inst = rr / a.nr;
-    const TwGlobal<T> tw{static_cast<const T*>(a.twS2)};
+    const TwGlobalProducts<T> tw{static_cast<const T*>(a.twS2)};
     T* base = static_cast<T*>(a.work);
+    auto row_of = [&](int part) { return base + ((inst * a.P + part) * a.nr + rb) * (int64_t)a.S + (int64_t)k1 * S2; };
     T v[A * E];
 #pragma unroll
     for (int aa = 0; aa < A; ++aa) {
-        const T* src = base + ((inst * A + aa) * a.nr + rb) * (int64_t)a.S + (int64_t)k1 * S2;
+        const T* src = row_of(aa);
 #pragma unroll
         for (int e = 0; e < E; ++e) v[aa * E + e] = valid ? src[tau + TT * e] : czero<T>();
     }
@@ -197,33 +209,57 @@ __device__ __forceinline__ void split_row_body(const SplitArgs& a, int64_t row, 
     // transform's exchanges put barriers in between); row 0 receives the result
     if (DISCARD && valid) {
 #pragma unroll
-        for (int aa = 1; aa < A; ++aa)
-            l2_discard(base + ((inst * A + aa) * a.nr + rb) * (int64_t)a.S + (int64_t)k1 * S2, (int64_t)S2 * sizeof(T),
-                       tau, TT);
+        for (int aa = 1; aa < A; ++aa) l2_discard(row_of(aa), (int64_t)S2 * sizeof(T), tau, TT);
     }
-    T p[E];
+    // mult at slot e: Hermitian residue spectra are real, so mult acts on the real parts
+    auto spec_in = [&](int e, auto* x) {
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-        if constexpr (KIND == KIND_HERMITIAN) {
-            // real residue spectra: mult acts on the real parts
-            const T x0 = v[e], x1 = v[E + e];
-            if constexpr (MULT == MULT_PRODUCT) {
-                p[e] = mk<T>(x0.x * x1.x, 0);
-            } else {
-                const T x2 = v[2 * E + e];
-                p[e] = mk<T>(x0.x * x1.x + x2.x * (x0.x + x1.x), 0);
+        for (int aa = 0; aa < A; ++aa) {
+            if constexpr (KIND == KIND_HERMITIAN) x[aa] = v[aa * E + e].x;
+            else x[aa] = v[aa * E + e];
+        }
+    };
+    using X = std::conditional_t<KIND == KIND_HERMITIAN, R, T>;
+    auto as_cplx = [](X y) -> T {
+        if constexpr (KIND == KIND_HERMITIAN) return mk<T>(y, R(0));
+        else return y;
+    };
+    if constexpr (MultShape<MULT>::OUT_SMEM) {
+#pragma unroll 1
+        for (int b = 0; b < B; ++b) {
+            T p[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                X x[A];
+                spec_in(e, x);
+                p[e] = as_cplx(mult_out<MULT, 1>(x, b));
             }
-        } else if constexpr (MULT == MULT_PRODUCT) {
-            p[e] = cmul(v[e], v[E + e]);
-        } else {
-            p[e] = cadd(cmul(v[e], v[E + e]), cmul(v[2 * E + e], cadd(v[e], v[E + e])));
+            fft_inverse<S2, E, 1>(p, sm, tw, tau);
+            if (valid) {
+                T* dst = row_of(b);
+#pragma unroll
+                for (int e = 0; e < E; ++e) dst[tau + TT * e] = p[e];
+            }
+        }
+    } else {
+        T p[B * E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            X x[A], y[B];
+            spec_in(e, x);
+            mult_point<MULT, 1, 1>(x, y);
+#pragma unroll
+            for (int b = 0; b < B; ++b) p[b * E + e] = as_cplx(y[b]);
+        }
+        fft_inverse<S2, E, B>(p, sm, tw, tau);
+        if (!valid) return;
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            T* dst = row_of(b);
+#pragma unroll
+            for (int e = 0; e < E; ++e) dst[tau + TT * e] = p[b * E + e];
         }
     }
-    fft_inverse<S2, E, 1>(p, sm, tw, tau);
-    if (!valid) return;
-    T* dst = base + ((inst * A + 0) * a.nr + rb) * (int64_t)a.S + (int64_t)k1 * S2;
-#pragma unroll
-    for (int e = 0; e < E; ++e) dst[tau + TT * e] = p[e];
 }
 
 // Rows: one group of S2/E threads per (instance, residue, row k1).
@@ -232,13 +268,12 @@ __global__ void __launch_bounds__(ConvLaunch<S2, E>::MAXT) split_row(const __gri
     using T = cplx<R>;
     using Sh = FftShape<S2, E>;
     constexpr int TT = Sh::T;
-    constexpr int A = MultShape<MULT>::A;
-    static_assert(MultShape<MULT>::B == 1, "single-output mults only");
+    constexpr int NX = MultShape<MULT>::NX;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int G = blockDim.x / TT;
     const int g = threadIdx.x / TT;
     const int tau = threadIdx.x - g * TT;
-    T* sm = reinterpret_cast<T*>(smem_raw) + (size_t)g * A * Sh::SMEM;
+    T* sm = reinterpret_cast<T*>(smem_raw) + (size_t)g * NX * Sh::SMEM;
     const int64_t row = (int64_t)blockIdx.x * G + g;
     const int64_t rows = a.count * a.nr * (int64_t)a.S1;
     split_row_body<R, S2, E, KIND, MULT>(a, row, row < rows, tau, sm);
@@ -252,14 +287,15 @@ __device__ __forceinline__ void split_store(T* p, T v, int accumulate) {
     __stcs(p, v);
 }
 
-// Backward column j2 of instance inst; all residues of the block accumulated.
+// Backward column j2 of output b of instance inst; all residues of the block
+// accumulated.
 template <class R, int S1, int KIND, bool COMP>
-__device__ __forceinline__ void split_colbwd_body(const SplitArgs& a, int64_t inst, int j2) {
+__device__ __forceinline__ void split_colbwd_body(const SplitArgs& a, int64_t inst, int b, int j2) {
     using T = cplx<R>;
     constexpr int NB = (KIND == KIND_HERMITIAN) ? 1 : 2;
     const T* twR = static_cast<const T*>(a.twR);
     const T* twS = static_cast<const T*>(a.twS);
-    const T* base = static_cast<const T*>(a.work) + inst * a.A * (int64_t)a.nr * a.S;
+    const T* base = static_cast<const T*>(a.work) + (inst * a.P + b) * (int64_t)a.nr * a.S;
     R s0[2 * S1], c0[COMP ? 2 * S1 : 1], s1[NB == 2 ? 2 * S1 : 1], c1[(NB == 2 && COMP) ? 2 * S1 : 1];
     R dummy = 0;
 #pragma unroll
@@ -282,11 +318,12 @@ __device__ __forceinline__ void split_colbwd_body(const SplitArgs& a, int64_t in
             v[k1] = k1 == 0 ? z : cmulc(z, tw[k1]);
         }
         dft_small<S1, true>(v);
-        const T* twr = twR + (int64_t)r * a.S;
-        const T tb = ldtw(twr + j2);                  // zeta_N^{r j2}
+        const TwistRow tr = twist_row(r, a.n);        // conjugate symmetry
+        const T* twr = twR + (int64_t)tr.row * a.S;
+        const T tb = twist_ld(twr + j2, tr.conj);     // zeta_N^{r j2}
 #pragma unroll
         for (int j1 = 0; j1 < S1; ++j1) {
-            T y = cmulc(v[j1], split_twist(twr, tb, j1, a.S2));
+            T y = cmulc(v[j1], split_twist(twr, tb, j1, a.S2, tr.conj));
             acc_add<R, COMP>(s0[2 * j1], COMP ? c0[2 * j1] : dummy, y.x);
             acc_add<R, COMP>(s0[2 * j1 + 1], COMP ? c0[2 * j1 + 1] : dummy, y.y);
             if constexpr (NB == 2) {
@@ -296,7 +333,7 @@ __device__ __forceinline__ void split_colbwd_body(const SplitArgs& a, int64_t in
             }
         }
     }
-    T* hout = static_cast<T*>(a.h) + inst * a.stride;
+    T* hout = static_cast<T*>(a.h[b]) + inst * a.stride;
     const R sc = R(a.invN);
 #pragma unroll
     for (int j1 = 0; j1 < S1; ++j1) {
@@ -331,7 +368,7 @@ __device__ __forceinline__ void split_colbwd_multi(const SplitArgs& a, int64_t i
     constexpr int NA = 2 * S1;
     const T* twR = static_cast<const T*>(a.twR);
     const T* twS = static_cast<const T*>(a.twS);
-    const T* base = static_cast<const T*>(a.work) + inst * a.A * (int64_t)a.nr * a.S;
+    const T* base = static_cast<const T*>(a.work) + inst * a.P * (int64_t)a.nr * a.S;   // output 0 (part 0)
     R s0[U][NA], c0[U][COMP ? NA : 1], s1[U][NB == 2 ? NA : 1], c1[U][(NB == 2 && COMP) ? NA : 1];
     R dummy = 0;
 #pragma unroll
@@ -354,7 +391,8 @@ __device__ __forceinline__ void split_colbwd_multi(const SplitArgs& a, int64_t i
 #pragma unroll
             for (int k1 = 0; k1 < S1; ++k1)
                 v[u][k1] = base[(int64_t)(r - a.r0) * a.S + (int64_t)k1 * a.S2 + j2base + u * jstep];
-        const T* twr = twR + (int64_t)r * a.S;
+        const TwistRow tr = twist_row(r, a.n);        // conjugate symmetry
+        const T* twr = twR + (int64_t)tr.row * a.S;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int j2 = j2base + u * jstep;
@@ -363,10 +401,10 @@ __device__ __forceinline__ void split_colbwd_multi(const SplitArgs& a, int64_t i
 #pragma unroll
             for (int k1 = 1; k1 < S1; ++k1) v[u][k1] = cmulc(v[u][k1], tw[k1]);
             dft_small<S1, true>(v[u]);
-            const T tb = ldtw(twr + j2);              // zeta_N^{r j2}
+            const T tb = twist_ld(twr + j2, tr.conj);  // zeta_N^{r j2}
 #pragma unroll
             for (int j1 = 0; j1 < S1; ++j1) {
-                T y = cmulc(v[u][j1], split_twist(twr, tb, j1, a.S2));
+                T y = cmulc(v[u][j1], split_twist(twr, tb, j1, a.S2, tr.conj));
                 acc_add<R, COMP>(s0[u][2 * j1], COMP ? c0[u][2 * j1] : dummy, y.x);
                 acc_add<R, COMP>(s0[u][2 * j1 + 1], COMP ? c0[u][2 * j1 + 1] : dummy, y.y);
                 if constexpr (NB == 2) {
@@ -377,7 +415,7 @@ __device__ __forceinline__ void split_colbwd_multi(const SplitArgs& a, int64_t i
             }
         }
     }
-    T* hout = static_cast<T*>(a.h) + inst * a.stride;
+    T* hout = static_cast<T*>(a.h[0]) + inst * a.stride;
     const R sc = R(a.invN);
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -407,12 +445,13 @@ __device__ __forceinline__ void split_colbwd_multi(const SplitArgs& a, int64_t i
     }
 }
 
-// Backward columns: one thread per (instance, j2).
+// Backward columns: one thread per (instance, output, j2).
 template <class R, int S1, int KIND, bool COMP>
 __global__ void __launch_bounds__(256) split_colbwd(const __grid_constant__ SplitArgs a) {
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (tid >= a.count * (int64_t)a.S2) return;
-    split_colbwd_body<R, S1, KIND, COMP>(a, tid / a.S2, (int)(tid % a.S2));
+    if (tid >= a.count * a.B * (int64_t)a.S2) return;
+    const int64_t ib = tid / a.S2;
+    split_colbwd_body<R, S1, KIND, COMP>(a, ib / a.B, (int)(ib % a.B), (int)(tid % a.S2));
 }
 
 }  // namespace hd

@@ -244,7 +244,7 @@ hd_status hd_autotune(const hd_desc* d, int64_t count, int reps, hd_candidate* o
     const int64_t Ls = d->kind == HD_HERMITIAN ? (d->L[0] + 1) / 2 : d->L[0];
     const size_t esz = d->dtype == HD_F64 ? 16 : 8;
     const size_t bytes = (size_t)count * (size_t)Ls * esz;
-    constexpr int kBufs = 3 + kMaxOut;
+    constexpr int kBufs = kMaxIn + kMaxOut;
     void* buf[kBufs] = {};
     hd_status st = HD_OK;
     if (d->A + d->B > kBufs) return HD_ERR_INVALID;
@@ -262,7 +262,8 @@ hd_status hd_autotune(const hd_desc* d, int64_t count, int reps, hd_candidate* o
             cands[i].ms = -1;
             continue;
         }
-        const void* f[3] = {buf[0], buf[1], buf[2]};
+        const void* f[kMaxIn];
+        for (int a = 0; a < kMaxIn; ++a) f[a] = buf[a];
         void* h[kMaxOut] = {};
         for (int b = 0; b < d->B && b < kMaxOut; ++b) h[b] = buf[d->A + b];
         t.clear();

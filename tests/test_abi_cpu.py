@@ -95,16 +95,14 @@ def test_enumerated_candidates_are_legal(hd, kind, dtype):
 
 
 def test_mult_counts_validated(hd):
-    """(A, B) must be the counts of the mult; the two-output mult has no split
-    path (transforms beyond the fused kernel) and no ragged form.  All of
-    these are refused before any device work."""
+    """(A, B) must be the counts of the mult, refused before any device work;
+    the two-output mult also runs on the split path (transforms beyond the
+    fused kernel)."""
     for A, B, mult in ((3, 2, None), (2, 2, "product"), (3, 1, "basdevant2"), (2, 3, None), (1, 1, "product")):
         with pytest.raises(hd.HdError) as e:
             hd.Plan(100, 199, A=A, B=B, mult=mult)
         assert e.value.name == "HD_ERR_INVALID", (A, B, mult)
-    with pytest.raises(hd.HdError) as e:
-        hd.Plan(40000, 79999, A=2, B=2)
-    assert e.value.name == "HD_ERR_UNSUPPORTED"
+    assert any(c["S"] > 4096 for c in hd.enumerate_candidates(L=40000, M=79999, A=2, B=2))
     # the default variant of FP32 two-output plans (E = 8, 255 registers) starts at S = 512;
     # smaller transforms are reachable through enumerated candidates
     with pytest.raises(hd.HdError) as e:
@@ -118,7 +116,7 @@ def test_mult_counts_validated(hd):
     assert hd.lib.hd_plan_create(ctypes.byref(out), 100, 199, 2, 3, 0, 0, 0, 0) == 1
     assert out.value is None
     cands = hd.enumerate_candidates(L=20000, M=39999, A=2, B=2)
-    assert cands == []
+    assert cands and all(c["S"] > 4096 and c["D"] == 1 for c in cands)   # the split path only
     assert hd.enumerate_candidates(L=4096, M=8191, A=2, B=2)
 
 
@@ -152,10 +150,32 @@ def test_cluster_candidates_enumerated(hd):
             assert c["D"] == 1                            # no cluster form of the split path
 
 
+def test_mhd3_counts_and_bounds(hd):
+    """The eight-output mult (A = 6, B = 8) has the binary dealiasing bounds,
+    is inferred from (A, B) = (6, 8) by hd_plan_create, and is refused with
+    other counts before any device work; long inputs take the split path."""
+    from oracle import params
+    for kind in ("complex", "centered", "hermitian"):
+        for L in (1, 100, 257):
+            assert hd.dealias_bound(kind, L, "mhd3") == params.dealias_bound(kind, L, "mhd3")
+    for A, B in ((3, 8), (6, 5), (6, 1)):
+        with pytest.raises(hd.HdError) as e:
+            hd.Plan(100, 199, A=A, B=B, mult="mhd3")
+        assert e.value.name == "HD_ERR_INVALID", (A, B)
+    split = hd.enumerate_candidates(L=20000, M=39999, A=6, B=8)
+    assert split and all(c["S"] > 4096 for c in split)
+    cands = hd.enumerate_candidates(L=300, M=599, A=6, B=8)
+    # fused transforms up to 1024 points (eight residue sums in shared memory), else the split path
+    assert cands and all((c["S"] <= 1024 or c["S"] > 4096) and c["D"] <= 1 for c in cands)
+    import ctypes
+    out = ctypes.c_void_p()
+    assert hd.lib.hd_plan_create(ctypes.byref(out), 100, 199, 6, 7, 0, 0, 0, 0) == 1   # HD_ERR_INVALID
+
+
 def test_basdevant3_counts_and_bounds(hd):
     """The five-output mult (A = 3, B = 5) has the binary dealiasing bounds,
-    is inferred from (A, B) = (3, 5), and is refused with other counts, on the
-    split path and in ragged batches, before any device work."""
+    is inferred from (A, B) = (3, 5), and is refused with other counts before
+    any device work; long inputs take the split path."""
     from oracle import params
     for kind in ("complex", "centered", "hermitian"):
         for L in (1, 100, 257):
@@ -164,8 +184,10 @@ def test_basdevant3_counts_and_bounds(hd):
         with pytest.raises(hd.HdError) as e:
             hd.Plan(100, 199, A=A, B=B, mult="basdevant3")
         assert e.value.name == "HD_ERR_INVALID", (A, B)
-    assert hd.enumerate_candidates(L=20000, M=39999, A=3, B=5) == []
-    assert all(c["S"] <= 4096 for c in hd.enumerate_candidates(L=3000, M=5999, A=3, B=5))
+    split = hd.enumerate_candidates(L=20000, M=39999, A=3, B=5)
+    assert split and all(c["S"] > 4096 for c in split)
+    # fused transforms up to 2048 points (five residue sums in shared memory), else the split path
+    assert all(c["S"] <= 2048 or c["S"] > 4096 for c in hd.enumerate_candidates(L=3000, M=5999, A=3, B=5))
     import ctypes
     out = ctypes.c_void_p()
     assert hd.lib.hd_plan_create(ctypes.byref(out), 100, 199, 3, 4, 0, 0, 0, 0) == 1   # HD_ERR_INVALID

@@ -137,10 +137,7 @@ def test_basdevant3_3d_whole_field(hd):
 
 
 def test_basdevant3_rejections(hd):
-    """Five outputs have no split path and no ragged form; (A, B) must match."""
-    with pytest.raises(hd.HdError) as e:
-        hd.Plan(40000, 79999, A=A, B=B)
-    assert e.value.name == "HD_ERR_UNSUPPORTED"
+    """(A, B) must match the mult."""
     with pytest.raises(hd.HdError) as e:
         hd.Plan(100, 199, A=2, B=5, mult="basdevant3")
     assert e.value.name == "HD_ERR_INVALID"

@@ -53,9 +53,13 @@ def brute_1d(fs, kind, mult):
         outs = [lin((1, conv(0, 1)), (1, conv(1, 2)), (1, conv(2, 0)))]
     elif mult == "basdevant2":        # u v, u^2 - v^2
         outs = [conv(0, 1), lin((1, conv(0, 0)), (-1, conv(1, 1)))]
-    else:                             # u v, v w, w u, u^2 - w^2, v^2 - w^2
+    elif mult == "basdevant3":        # u v, v w, w u, u^2 - w^2, v^2 - w^2
         outs = [conv(0, 1), conv(1, 2), conv(2, 0), lin((1, conv(0, 0)), (-1, conv(2, 2))),
                 lin((1, conv(1, 1)), (-1, conv(2, 2)))]
+    else:                             # mhd3: inputs z+ = (0, 1, 2), z- = (3, 4, 5); T_ij = z-_i z+_j
+        T = {(i, j): conv(3 + i, j) for i in range(3) for j in range(3)}
+        outs = [T[0, 1], T[0, 2], T[1, 0], T[1, 2], T[2, 0], T[2, 1],
+                lin((1, T[0, 0]), (-1, T[2, 2])), lin((1, T[1, 1]), (-1, T[2, 2]))]
     n = len(fs[0])
     if kind == "complex":
         keys = range(n)
@@ -67,7 +71,7 @@ def brute_1d(fs, kind, mult):
     return res[0] if len(outs) == 1 else res
 
 
-ALL_MULTS = ["product", "sum_pairs3", "basdevant2", "basdevant3"]
+ALL_MULTS = ["product", "sum_pairs3", "basdevant2", "basdevant3", "mhd3"]
 
 
 @pytest.mark.parametrize("kind", ["complex", "centered", "hermitian"])
@@ -294,7 +298,35 @@ def test_basdevant_special_cases(kind):
     assert np.allclose(b3[3] - b3[4], b[1], atol=1e-13)
 
 
-@pytest.mark.parametrize("mult", ["basdevant2", "basdevant3"])
+@pytest.mark.parametrize("kind", ["complex", "centered", "hermitian"])
+def test_mhd_special_cases(kind):
+    """The MHD mult (traceless part of z-_i z+_j): with z+ = z- = u it holds the
+    3D Basdevant outputs of u (T symmetric, so T_10, T_21, T_02 repeat T_01,
+    T_12, T_20); swapping z+ and z- transposes T; z- = 0 gives zeros."""
+    L = 17
+    if kind == "hermitian":
+        u = list(inputs.hermitian_1d(3, L, 61))
+        w = list(inputs.hermitian_1d(3, L, 62))
+    else:
+        u = list(inputs.uniform_complex((3, L), 61))
+        w = list(inputs.uniform_complex((3, L), 62))
+    b3 = direct.conv1d(u, kind, "basdevant3")
+    m = direct.conv1d(u + u, kind, "mhd3")
+    assert m.shape == (8, len(u[0]))
+    for k, b in ((0, 0), (3, 1), (4, 2), (6, 3), (7, 4)):     # T_01, T_12, T_20, T_00 - T_22, T_11 - T_22
+        assert np.allclose(m[k], b3[b], atol=1e-13), (k, b)
+    for a, b in ((0, 2), (3, 5), (4, 1)):                      # T_01 = T_10, T_12 = T_21, T_20 = T_02
+        assert np.allclose(m[a], m[b], atol=1e-13)
+    mw = direct.conv1d(u + w, kind, "mhd3")
+    mt = direct.conv1d(w + u, kind, "mhd3")
+    for a, b in ((0, 2), (1, 4), (3, 5)):                      # transposed off-diagonal entries
+        assert np.allclose(mw[a], mt[b], atol=1e-13)
+    assert np.allclose(mw[6], mt[6], atol=1e-13) and np.allclose(mw[7], mt[7], atol=1e-13)
+    z = [np.zeros_like(x) for x in u]
+    assert not np.any(direct.conv1d(u + z, kind, "mhd3"))
+
+
+@pytest.mark.parametrize("mult", ["basdevant2", "basdevant3", "mhd3"])
 def test_multi_output_batch_points_and_nd(mult):
     """B > 1: the batch, point and N-D forms agree with the 1D definition and
     the explicit FFT convolution, output by output."""

@@ -54,11 +54,11 @@ def test_steps_sum_pairs3(kind):
 
 
 @pytest.mark.parametrize("kind", ["complex", "centered", "hermitian"])
-@pytest.mark.parametrize("mult", ["basdevant2", "basdevant3"])
+@pytest.mark.parametrize("mult", ["basdevant2", "basdevant3", "mhd3"])
 def test_steps_multi_output(kind, mult):
     """B > 1 outputs: each accumulates its own residue contributions; the
     algorithm equals the definition for every m."""
-    A = 2 if mult == "basdevant2" else 3
+    A = direct.MULTS[mult]
     for L in (4, 7):
         fs = _fs(kind, L, 88, A=A)
         ref = direct.conv1d(fs, kind, mult)

@@ -41,6 +41,9 @@ def mult_outputs(F, mult):
         return [F[0] * F[1] + F[2] * (F[0] + F[1])]
     if mult == "basdevant2":
         return [F[0] * F[1], (F[0] + F[1]) * (F[0] - F[1])]
+    if mult == "mhd3":
+        p0, p1, p2, m0, m1, m2 = F
+        return [m0 * p1, m0 * p2, m1 * p0, m1 * p2, m2 * p0, m2 * p1, m0 * p0 - m2 * p2, m1 * p1 - m2 * p2]
     raise ValueError(mult)
 
 
@@ -71,9 +74,13 @@ def blocks(kind, f, S):
     return b0, b1
 
 
-def convolve_formulation(fs, kind, mult, m, p, q, slip=None):
+def convolve_formulation(fs, kind, mult, m, p, q, slip=None, conj_sym=False):
     """slip (planted mistakes): "fold_factor" (centered block-1 factor not
-    conjugated) or "sign" (forward transform with -zeta)."""
+    conjugated), "sign" (forward transform with -zeta) or "csym_backward" (the
+    paired residue's own backward twist after a conjugated forward one).
+    conj_sym: residues r > n/2 (complex and centered kinds) twist with the
+    conjugated twists of residue n - r, in both directions (Section 6.3, as the
+    kernels do: their spectra come out shifted by one frequency)."""
     S, n = geometry(kind, m, p, q)
     N = n * S
     fs = [np.asarray(f, complex) for f in fs]
@@ -85,11 +92,16 @@ def convolve_formulation(fs, kind, mult, m, p, q, slip=None):
     j = np.arange(S)
     bl = [blocks(kind, f, S) for f in fs]
 
+    def twist(r):
+        if conj_sym and 2 * r > n:
+            return np.conj(zeta(N, (n - r) * j))
+        return zeta(N, r * j)
+
     def twisted(r):
         cr = zeta(N, r * S)
         if kind != "complex" and slip != "fold_factor":
             cr = np.conj(cr)
-        return [(b0 + cr * b1) * zeta(N, r * j) for b0, b1 in bl], cr
+        return [(b0 + cr * b1) * twist(r) for b0, b1 in bl], cr
 
     if kind != "hermitian":
         for r in range(n):
@@ -97,8 +109,9 @@ def convolve_formulation(fs, kind, mult, m, p, q, slip=None):
             # forward with +zeta (Eq. forStan): F_l = sum_j zeta_S^{j l} W_j
             F = [np.fft.fft(w) if slip == "sign" else np.fft.ifft(w) * S for w in W]
             Y = [np.fft.fft(h) for h in mult_outputs(F, mult)]   # unnormalized inverse: zeta^{-}
+            tb = zeta(N, r * j) if slip == "csym_backward" else twist(r)
             for b in range(B):
-                y = Y[b] * np.conj(zeta(N, r * j))
+                y = Y[b] * np.conj(tb)
                 acc0[b] += y
                 acc1[b] += y * np.conj(cr)
     else:
@@ -186,4 +199,39 @@ def test_formulation_planted_slips_fail(slip):
     assert params.derive("centered", L, M, m) == (p, q, 3)
     assert np.allclose(convolve_formulation(fs, "centered", "product", m, p, q), ref, atol=1e-10)
     bad = convolve_formulation(fs, "centered", "product", m, p, q, slip=slip)
+    assert not np.allclose(bad, ref, atol=1e-6)
+
+
+@pytest.mark.parametrize("kind", ["complex", "centered"])
+@pytest.mark.parametrize("mult", ["product", "sum_pairs3", "basdevant2", "mhd3"])
+def test_conjugate_symmetry_pairs_equal_definition(kind, mult):
+    """Conjugate symmetry (Section 6.3) as the kernels use it: residue r > n/2
+    takes the conjugated twists of residue n - r in both directions; every plan
+    with n >= 3 (where some residue is paired) still gives the definition."""
+    A = direct.MULTS[mult]
+    checked = 0
+    for L in (3, 8, 13, 21):
+        fs = stored(kind, L, A, 500 + L)
+        ref = direct.conv1d(fs, kind, mult)
+        bound = params.dealias_bound(kind, L, mult)
+        for M in (bound, 2 * L + 5, 3 * L + 1):
+            for m, p, q in legal_plans(kind, L, M):
+                S, n = geometry(kind, m, p, q)
+                if n < 3:
+                    continue
+                got = convolve_formulation(fs, kind, mult, m, p, q, conj_sym=True)
+                assert np.allclose(got, ref, atol=1e-10), (kind, mult, L, M, m, p, q)
+                checked += 1
+    assert checked >= 10
+
+
+def test_conjugate_symmetry_planted_slip_fails():
+    """Conjugated forward twists with the paired residue's own backward twist
+    (the one-frequency shift left in place) miss the definition."""
+    L, M = 13, 20
+    fs = stored("centered", L, 2, 77)
+    ref = direct.conv1d(fs, "centered")
+    m, p, q = 4, 4, 6                        # S = 8, n = 3: residue 2 pairs with residue 1
+    assert np.allclose(convolve_formulation(fs, "centered", "product", m, p, q, conj_sym=True), ref, atol=1e-10)
+    bad = convolve_formulation(fs, "centered", "product", m, p, q, slip="csym_backward", conj_sym=True)
     assert not np.allclose(bad, ref, atol=1e-6)

@@ -100,3 +100,42 @@ def test_split_residue_blocks(hd, kind, L, A):
             with pytest.raises(hd.HdError) as e:
                 plan.convolve_batched(d, d[0], 3, fs[0].shape[1])
             assert e.value.name == "HD_ERR_INVALID"
+
+
+@pytest.mark.parametrize("mult,kind,L", [("basdevant2", "complex", 9000), ("basdevant2", "hermitian", 20001),
+                                         ("basdevant3", "centered", 9999), ("mhd3", "complex", 6000),
+                                         ("mhd3", "hermitian", 12001)])
+def test_split_multi_output(hd, mult, kind, L):
+    """B > 1 outputs on the split path: the rows form the B output spectra (two
+    together, or one at a time for five and eight) and write output b over part
+    b of the work buffer, which holds max(A, B) parts per residue; every output
+    of every candidate against the FP64 oracle, FP32 rel-L2 <= 1e-5 per output
+    and instance, and one FP64 case exact after rint on integer inputs."""
+    import torch
+    A, B = {"basdevant2": (2, 2), "basdevant3": (3, 5), "mhd3": (6, 8)}[mult]
+    M = params.dealias_bound(kind, L, mult) + 11
+    fs = make_inputs(kind, L, A, 2, 950 + L)
+    ref = cdirect.conv1d_batch(fs, L, kind, mult)
+    cands = split_cands(hd, L=L, M=M, A=A, B=B, kind=kind)
+    assert cands, "no split candidate"
+    for c in cands[:3]:
+        with hd.Plan(L, M, A=A, B=B, kind=kind, candidate=c) as plan:
+            assert plan.params()["scratch_bytes"] % (max(A, B) * c["S"] * 8) == 0
+            d = [torch.from_numpy(f.astype(np.complex64)).cuda() for f in fs]
+            outs = [torch.zeros_like(d[0]) for _ in range(B)]
+            plan.convolve_batched(d, outs, 2, fs[0].shape[1])
+            torch.cuda.synchronize()
+            for b in range(B):
+                e = rel_l2_rows(outs[b].cpu().numpy(), ref[b])
+                assert e <= 1e-5, (c, b, e)
+    if mult == "basdevant2" and kind == "complex":
+        fi = make_inputs(kind, 4096, A, 2, 960, integer=True)
+        refi = cdirect.conv1d_batch(fi, 4096, kind, mult)
+        with hd.Plan(4096, 8191, A=A, B=B, m=8192, p=1, q=1, dtype="f64") as plan:
+            d = [torch.from_numpy(f).cuda() for f in fi]
+            outs = [torch.zeros_like(d[0]) for _ in range(B)]
+            plan.convolve_batched(d, outs, 2, 4096)
+            torch.cuda.synchronize()
+            for b in range(B):
+                g = outs[b].cpu().numpy()
+                assert np.array_equal(np.rint(g.real) + 1j * np.rint(g.imag), refi[b]), b
