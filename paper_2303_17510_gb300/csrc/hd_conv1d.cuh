@@ -560,9 +560,13 @@ __device__ __forceinline__ void conv1d_body(const ConvArgs& a, int64_t inst, boo
 // One thread group of T = S/E threads per convolution; G = blockDim.x / T
 // groups per CTA; shared memory per group: the A staged inputs (ls_pad values
 // each), then A padded FFT exchange buffers.  MINB: CTAs per SM the register
-// allocation must allow (1: up to 255 registers for 256 threads; 2: at most 128).
+// allocation must allow (1: up to 255 registers for 256 threads; 2: at most
+// 128; the MINB = 2 variants up to S = 256 are held to three CTAs per SM, 80
+// registers: their rows are short, and the third CTA hides more of the staging
+// loads, 2 % on the 256^3 Hermitian plan, whose inner rows are S = 128).
 template <class R, int S, int E, int KIND, int MULT, int NB, bool COMP, int MINB>
-__global__ void __launch_bounds__(ConvLaunch<S, E>::MAXT, MINB) conv1d_kernel(const __grid_constant__ ConvArgs a) {
+__global__ void __launch_bounds__(ConvLaunch<S, E>::MAXT, (MINB == 2 && S <= 256) ? 3 : MINB)
+    conv1d_kernel(const __grid_constant__ ConvArgs a) {
     using T = cplx<R>;
     using Sh = FftShape<S, E>;
     constexpr int TT = Sh::T;
