@@ -71,14 +71,14 @@ enum { HD_F32 = 0, HD_F64 = 1 };
  * u^2 - v^2 of its nonlinear term in Basdevant's form (Section 9 counts
  * A = B = 2).  Binary bound; 1D plans (fused kernel, S up to 4096 FP32 /
  * 2048 FP64; FP32 from S = 512 on unless a candidate of hd_enumerate_candidates
- * is given) and 2D/3D plans.
+ * is given; larger transforms on the split path) and 2D/3D plans.
  * HD_MULT_BASDEVANT3: A = 3, B = 5, (F1 F2, F2 F3, F3 F1, F1^2 - F3^2,
  * F2^2 - F3^2): from the velocity components u, v, w of a 3D incompressible
  * flow, the products u v, v w, w u, u^2 - w^2 and v^2 - w^2 of its nonlinear
  * term in Basdevant's form (Section 9 counts A = 3, B = 5).  Binary bound; 1D
  * plans (fused kernel: the five residue sums live in shared memory, so FP32
- * transforms up to S = 1024 and FP64 up to 512 for short rows) and 2D/3D
- * plans; no split path.
+ * transforms up to S = 1024 and FP64 up to 512 for short rows; larger ones on
+ * the split path) and 2D/3D plans.
  * HD_MULT_MHD3: A = 6, B = 8: from the Elsasser components z+ = u + b
  * (inputs 0, 1, 2) and z- = u - b (inputs 3, 4, 5) of a 3D incompressible
  * magnetohydrodynamic flow, the eight entries of the traceless part of the
@@ -87,7 +87,8 @@ enum { HD_F32 = 0, HD_F64 = 1 };
  * form; the trace, like that of Basdevant's velocity tensor, goes into the
  * pressure).  Binary bound; 1D plans (fused kernel: the eight residue sums
  * live in shared memory, so FP32 transforms up to S = 1024 and FP64 up to 512
- * for short rows) and 2D/3D plans; no split path. */
+ * for short rows; larger ones on the split path) and 2D/3D plans.  Ragged
+ * batches take the single-output mults only. */
 enum { HD_MULT_PRODUCT = 0, HD_MULT_SUM_PAIRS3 = 1, HD_MULT_BASDEVANT2 = 2, HD_MULT_BASDEVANT3 = 3, HD_MULT_MHD3 = 4 };
 
 typedef struct hd_plan hd_plan;
