@@ -48,9 +48,12 @@ struct ColShape {
 // Forward: input blockIdx.y, all nr residues of the block: the column tile is
 // read once (both folded blocks kept in registers), then per residue fold +
 // twist, FFT along x, spectral values to the work buffer.  Residue 0 (r0 = 0)
-// has unit twists.
+// has unit twists.  Tiles of 256 threads (S <= 128) are held to two CTAs per
+// SM (128 registers, no spills): left alone the compiler took 164 registers,
+// one CTA per SM, and the 256^3 Hermitian plan ran 10 % slower.
 template <class R, int S, int E, int KIND>
-__global__ void __launch_bounds__(ColShape<S, E>::THREADS) col_forward(const __grid_constant__ ColArgs a) {
+__global__ void __launch_bounds__(ColShape<S, E>::THREADS, ColShape<S, E>::THREADS <= 256 ? 2 : 1)
+    col_forward(const __grid_constant__ ColArgs a) {
     using T = cplx<R>;
     using CS = ColShape<S, E>;
     constexpr int TY = CS::TY;
