@@ -190,3 +190,69 @@ def test_two_gloo_ranks_residue_sharding(tmp_path):
         sl = len(padded) // world
         for r in range(world):
             assert np.max(np.abs(res[r][kind][2] - padded[r * sl:(r + 1) * sl])) < 1e-12 * max(1.0, np.max(np.abs(ref)))
+
+
+class _OraclePlan:
+    """Stand-in for a plan on the CPU: convolve_residues computes the oracle's
+    partial sums (steps.convolve / convolveX over a residue range), so the
+    sharding glue can run with gloo ranks and no GPU."""
+
+    def __init__(self, kind, L, M, m, mult):
+        self.kind, self.L, self.M, self.m, self.mult = kind, L, M, m, mult
+        self.residues = params.derive(kind, L, M, m)[2]
+
+    def convolve_residues(self, fs, h, r0, r1, count=1, batch_stride=0, stream=None):
+        import torch
+        f = [x.numpy() for x in fs]
+        if self.kind == "complex":
+            y = steps.convolve(f, self.L, self.M, self.m, self.mult, residues=(r0, r1))
+        else:
+            y = steps.convolveX(f, self.L, self.M, self.m, self.kind, self.mult, residues=(r0, r1))
+        if isinstance(h, (list, tuple)):
+            for b, t in enumerate(h):
+                t.copy_(torch.from_numpy(y[b]))
+        else:
+            h.copy_(torch.from_numpy(y))
+
+
+def _rank_main_sharded(rank, world, port, out_dir):
+    os.environ.update(RANK=str(rank), WORLD_SIZE=str(world), MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    sys.path.insert(0, ROOT)
+    import torch
+    import torch.distributed as dist
+    sharding = _sharding()
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    res = {}
+    for kind, L, M, m, mult in (("complex", 16, 31, 8, "product"), ("centered", 17, 30, 4, "basdevant2"),
+                                ("complex", 13, 40, 8, "mhd3")):
+        A = direct.MULTS[mult]
+        fs = [torch.from_numpy(inputs.uniform_complex(L, 900 + a)) for a in range(A)]
+        plan = _OraclePlan(kind, L, M, m, mult)
+        B = direct.OUTPUTS[mult]
+        if B == 1:
+            h = torch.zeros(L, dtype=torch.complex128)
+            sharding.convolve_sharded(plan, fs, h)
+            res[mult] = h.numpy()
+        else:
+            hs = [torch.zeros(L, dtype=torch.complex128) for _ in range(B)]
+            sharding.convolve_sharded(plan, fs, hs)
+            res[mult] = np.stack([t.numpy() for t in hs])
+    dist.barrier()
+    dist.destroy_process_group()
+    np.save(os.path.join(out_dir, f"s{rank}.npy"), np.array([res], dtype=object), allow_pickle=True)
+
+
+@pytest.mark.timeout(180)
+def test_two_gloo_ranks_convolve_sharded_single_and_multi_output(tmp_path):
+    """sharding.convolve_sharded over two gloo ranks with the oracle standing in
+    for the plan: one output (reduced in place) and the two- and eight-output
+    mults (each output all-reduced) give the whole convolution on every rank."""
+    world = 2
+    mp.start_processes(_rank_main_sharded, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True,
+                       start_method="spawn")
+    res = [np.load(tmp_path / f"s{r}.npy", allow_pickle=True)[0] for r in range(world)]
+    for kind, L, mult in (("complex", 16, "product"), ("centered", 17, "basdevant2"), ("complex", 13, "mhd3")):
+        A = direct.MULTS[mult]
+        ref = direct.conv1d([inputs.uniform_complex(L, 900 + a) for a in range(A)], kind, mult)
+        for r in range(world):
+            assert np.max(np.abs(res[r][mult] - ref)) < 1e-12 * max(1.0, np.max(np.abs(ref))), (mult, r)
